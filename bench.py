@@ -1,0 +1,394 @@
+#!/usr/bin/env python
+"""Benchmark of the checkerboard SU(3) gauge sweep on GB300.
+
+Workload: SU(3) Wilson action on a 64^3 x 16 lattice (4.2M sites), beta 6.2,
+constant lambda3 background field with flux quantum n = 1, hot start, links
+stored in FP32 (12 reals per link, third row rebuilt).  One step = one working
+sweep: 1 Cabibbo-Marinari heat-bath pass + 4 overrelaxation passes + FP64
+reunitarization + plaquette / Polyakov-loop measurement (FP64 sums).  The
+links (805 MB) are larger than L2 (129 MB), so no L2 flush is needed.
+
+Metric: link updates per second (one heat-bath or one overrelaxation update of
+one link = one update).  Prints one JSON line.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Under torchrun (N > 1) every rank runs an independent replica (its own seed)
+and rank 0 reports the units of all ranks over the slowest rank's time.
+"""
+from __future__ import annotations
+
+import argparse
+import ctypes
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import workloads  # noqa: E402
+
+METRIC = "link updates/sec and HBM GB/s (% of peak), FP32-batched vs FP64 plain, |dP|<=1e-6"
+UNIT = "link updates/s"
+# link bytes per storage; algorithmic traffic per link update is 9 link
+# transfers (3V links of the other directions, V/2 opposite-parity links of the
+# same direction, V/2 read + V/2 written, for V/2 updates per phase).
+LINK_BYTES = {(3, 1): 48, (3, 0): 144, (2, 1): 16, (2, 0): 32}
+TRANSFERS_PER_UPDATE = 9
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=100)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extras", action="store_true", help="skip the FP64-plain side measurement")
+    ap.add_argument("--Ns", type=int, default=None, help="override the spatial extent (small profiling cases)")
+    ap.add_argument("--Nt", type=int, default=None, help="override the time extent (small profiling cases)")
+    return ap.parse_args()
+
+
+def dist_info():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def load_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def kernel_source_sha():
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_1310_7087_gb300", "csrc")
+    for name in sorted(os.listdir(csrc)):
+        if name.endswith((".cu", ".cuh", ".h")):
+            with open(os.path.join(csrc, name), "rb") as f:
+                h.update(name.encode() + f.read())
+    return h.hexdigest()[:16]
+
+
+def ncu_traffic(kernel_kind):
+    """DRAM bytes per launch of the dominant kernel from the committed ncu
+    summary, if it was taken on the current kernel sources; else None."""
+    path = os.path.join(ROOT, "profiles", "ncu_traffic.json")
+    if not os.path.exists(path):
+        return None
+    with open(path) as f:
+        d = json.load(f)
+    e = d.get(kernel_kind)
+    if not e or e.get("source_sha") != kernel_source_sha():
+        return None
+    return e.get("dram_bytes_per_launch")
+
+
+class ClockSampler:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed
+    region."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+    NAMES = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+
+    def __init__(self, device_index: int):
+        self.samples = []
+        self.window = None
+        self.proc = None
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(device_index), "--query-gpu=" + self.FIELDS,
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 8:
+                self.samples.append((time.time(), parts))
+
+    def start(self):
+        self.t0 = time.time()
+
+    def stop(self):
+        self.t1 = time.time()
+        time.sleep(0.25)
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=2)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        inside = [p for t, p in self.samples if self.t0 - 0.1 <= t <= self.t1 + 0.1]
+        if not inside:
+            inside = [p for _, p in self.samples]
+        if not inside:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+
+        def num(x):
+            try:
+                return float(x)
+            except ValueError:
+                return None
+        sm = [num(p[1]) for p in inside if num(p[1]) is not None]
+        mx = [num(p[2]) for p in inside if num(p[2]) is not None]
+        reasons = sorted({n for p in inside for n, v in zip(self.NAMES, p[4:8]) if v.lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(inside)}
+
+
+def cpu_baseline_oracle(w):
+    """The oracle as it stands, on all host cores, on a bounded sample of the
+    same workload: one heat-bath pass, one overrelaxation pass, one
+    reunitarization and one measurement of the full lattice, combined with the
+    sweep's 1 : 4 pass mix."""
+    import oracle
+    oracle.build()
+    L = oracle.OracleLattice(w.group, w.Ns, w.Nt, w.beta, w.flux, w.nhit, 0)
+    L.hot_start(w.seed)
+    t = {}
+    t0 = time.perf_counter()
+    for p in range(2):
+        for mu in range(4):
+            L.phase(oracle.HEATBATH, p, mu, w.seed)
+    t["hb"] = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    for p in range(2):
+        for mu in range(4):
+            L.phase(oracle.OVERRELAX, p, mu, w.seed)
+    t["or"] = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    L.reunitarize()
+    t["re"] = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    L.measure()
+    t["me"] = time.perf_counter() - t0
+    L.close()
+    sweep_s = t["hb"] + w.n_or * t["or"] + t["re"] + t["me"]
+    lu = (1 + w.n_or) * 4 * w.volume
+    return {"value": lu / sweep_s, "unit": UNIT, "cores": oracle.get_threads(), "kind": "oracle",
+            "sample": "one HB pass, one OR pass, one reunitarization and one measurement of the full "
+                      "%s lattice (%.1f s of CPU work), combined as 1 HB + %d OR per sweep"
+                      % (w.name, sum(t.values()), w.n_or),
+            "seconds": {k: round(v, 3) for k, v in t.items()}}
+
+
+def run_reference(args, w):
+    """Reference arm: the FP64 CPU oracle timed on the host cores."""
+    world, rank, _ = dist_info()
+    if rank != 0:
+        return 0
+    import oracle
+    oracle.build()
+    L = oracle.OracleLattice(w.group, w.Ns, w.Nt, w.beta, w.flux, w.nhit, 0)
+    L.hot_start(w.seed)
+    Vh = w.volume // 2
+    schedule = []
+    for i in range(1 + w.n_or):
+        for p in range(2):
+            for mu in range(4):
+                schedule.append((oracle.HEATBATH if i == 0 else oracle.OVERRELAX, p, mu))
+    # one step = one checkerboard phase, cycling through a sweep's phases in
+    # order (8 heat-bath phases, then 8 n_or overrelaxation phases)
+    k = 0
+    for _ in range(args.warmup):
+        L.phase(*schedule[k % len(schedule)], w.seed)
+        k += 1
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        L.phase(*schedule[k % len(schedule)], w.seed)
+        k += 1
+    dt = time.perf_counter() - t0
+    L.close()
+    value = args.steps * Vh / dt
+    cores = oracle.get_threads()
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic (hot start, Philox seed %d)" % w.seed,
+            "config": config_of(w, "FP64 18-real (oracle)"),
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": "one checkerboard phase (%d link updates) per step, cycling "
+                                       "through the sweep's HB and OR phases" % Vh},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def config_of(w, storage):
+    return {"workload": w.name, "group": "SU(%d)" % w.group, "lattice": "%d^3x%d" % (w.Ns, w.Nt),
+            "sites": w.volume, "beta": w.beta, "flux": w.flux, "storage": storage,
+            "sweep": "1 HB + %d OR + reunitarization + measurement" % w.n_or,
+            "l2": "links larger than L2 (no flush between steps)"}
+
+
+def main():
+    args = parse()
+    w = workloads.SU3_64x16
+    if args.Ns or args.Nt:
+        import dataclasses
+        Ns, Nt = args.Ns or w.Ns, args.Nt or w.Nt
+        w = dataclasses.replace(w, Ns=Ns, Nt=Nt, name="su3_%d^3x%d_b%g_n%d" % (Ns, Nt, w.beta, w.flux))
+    if args.impl == "reference":
+        return run_reference(args, w)
+
+    import torch
+    world, rank, local = dist_info()
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    from paper_1310_7087_gb300 import build
+    build.build()
+    import paper_1310_7087_gb300 as q
+
+    stream = torch.cuda.current_stream()
+    seed = w.seed + 1000 * rank
+    lat = q.Lattice(w.group, w.Ns, w.Nt, w.beta, w.flux, q.QCD_FP32_COMPRESSED, q.QCD_HOT, seed, stream)
+    h = lat.h
+    lu_per_step = (1 + w.n_or) * 4 * w.volume
+
+    def step():
+        q.qcd_sweep(h, 1, w.n_or, seed)
+        return q.qcd_measure(h)
+
+    for _ in range(args.warmup):
+        step()
+    q.qcd_set_profiling(h, True)
+    clocks = ClockSampler(local)
+    time.sleep(0.3)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    clocks.start()
+    e0.record(stream)
+    last = None
+    for _ in range(args.steps):
+        last = step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    clocks.stop()
+    if dist:
+        dist.barrier()
+    t_ms = e0.elapsed_time(e1)
+    prof_ms, prof_n = q.qcd_get_profile(h)
+    q.qcd_set_profiling(h, False)
+    if dist:
+        t = torch.tensor([t_ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        t_ms = float(t.item())
+    value = lu_per_step * args.steps * world / (t_ms / 1e3)
+
+    # roofline of the dominant kernel (largest share of the timed kernel time)
+    names = ["heatbath_phase", "overrelax_phase", "reunitarize", "measure"]
+    dom = max(range(2), key=lambda k: prof_ms[k])
+    per_launch_ms = prof_ms[dom] / max(1, prof_n[dom])
+    link_b = LINK_BYTES[(w.group, 1)]
+    alg_bytes = TRANSFERS_PER_UPDATE * link_b * (w.volume // 2)
+    peak, peak_src = load_peaks()
+    achieved = alg_bytes / (per_launch_ms / 1e3) / 1e9
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                "traffic": ncu_traffic(names[dom]), "kernel": names[dom],
+                "peak_source": "%s (MEASURED_PEAKS.json hbm_gbs)" % peak_src if peak_src == "measured"
+                else "fallback 6.8 TB/s",
+                "alg_bytes_per_launch": alg_bytes, "avg_launch_ms": per_launch_ms,
+                "kernel_ms": {n: round(m, 3) for n, m in zip(names, prof_ms)},
+                "kernel_launches": {n: int(c) for n, c in zip(names, prof_n)}}
+
+    # end to end through the C ABI: per step, the configuration comes from
+    # pinned host memory and the measurement goes back to the host
+    nbytes = q.qcd_link_bytes(h)
+    host = torch.empty(nbytes, dtype=torch.uint8, pin_memory=True)
+    q.qcd_copy_links_out(h, host.data_ptr(), nbytes)
+    e2e_steps = max(3, min(args.steps, 20))
+    q.qcd_copy_links_in(h, host.data_ptr(), nbytes)
+    step()
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        q.qcd_copy_links_in(h, host.data_ptr(), nbytes)
+        step()
+    torch.cuda.synchronize()
+    t_e2e = time.perf_counter() - t0
+    if dist:
+        t = torch.tensor([t_e2e], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        t_e2e = float(t.item())
+    e2e = {"value": lu_per_step * e2e_steps * world / t_e2e, "unit": UNIT, "h2d_bytes_per_step": nbytes,
+           "d2h_bytes_per_step": 5 * 8, "steps": e2e_steps}
+
+    extras = {}
+    if not args.no_extras:
+        # FP64-plain single lattice, same workload, for the FP32-vs-FP64 comparison
+        lat64 = q.Lattice(w.group, w.Ns, w.Nt, w.beta, w.flux, q.QCD_FP64_PLAIN, q.QCD_HOT, seed, stream)
+        q.qcd_sweep(lat64.h, 1, w.n_or, seed)
+        q.qcd_measure(lat64.h)
+        q.qcd_set_profiling(lat64.h, True)
+        torch.cuda.synchronize()
+        f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        n64 = 2
+        f0.record(stream)
+        for _ in range(n64):
+            q.qcd_sweep(lat64.h, 1, w.n_or, seed)
+            q.qcd_measure(lat64.h)
+        f1.record(stream)
+        torch.cuda.synchronize()
+        ms64 = f0.elapsed_time(f1) / n64
+        pm, pn = q.qcd_get_profile(lat64.h)
+        extras["fp64_plain"] = {"value": lu_per_step / (ms64 / 1e3), "unit": UNIT, "ms_per_step": ms64,
+                                "storage": "FP64 18-real", "bound": "fp64 alu",
+                                "kernel_ms_per_step": {n: round(m / n64, 3) for n, m in zip(names, pm)},
+                                "fp32_speedup": (lu_per_step * args.steps / (t_ms / 1e3)) /
+                                                (lu_per_step / (ms64 / 1e3))}
+        lat64.close()
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline_oracle(w)
+
+    launches = int(sum(prof_n))
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": t_ms / args.steps, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+                "data": "synthetic: hot start (Haar links from Philox seed %d), no dataset" % w.seed,
+                "config": dict(config_of(w, "FP32 12-real (rows 1-2, row 3 rebuilt)"),
+                               parallelism="replicas" if world > 1 else "single GPU",
+                               block=q.qcd_get_block(h)),
+                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks.summary(),
+                "gpu_launches": launches, "last_measurement": {"plaquette": last[0], "polyakov": last[1]},
+                **extras}
+        print(json.dumps(line), flush=True)
+    lat.close()
+    if dist:
+        dist.barrier()
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

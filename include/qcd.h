@@ -1,0 +1,171 @@
+/*
+ * qcd.h -- C ABI of libqcdgb300: the checkerboard Monte Carlo sweep of pure
+ * SU(2)/SU(3) Wilson lattice gauge theory at finite temperature in a constant
+ * Abelian chromomagnetic background field, on one NVIDIA GB300 (sm_103a).
+ *
+ * What the calls compute.  The paper (QCDGPU, Demchik & Kolomoyets) describes
+ * SU(N) gluodynamics in an external field at finite temperature (abstract,
+ * sec. 1), links stored as N x N matrices split into 4-vectors with the site
+ * index fastest (sec. 3.3), (pseudo)heat-bath updates of the even and odd
+ * checkerboard halves (sec. 3.3), hot start, NHIT = 10 tries and
+ * reunitarization (sec. 5), and plaquette / Polyakov-loop measurements (sec. 1,
+ * sec. 5).  It prints no formulas; the library implements the textbook methods
+ * those passages name:
+ *   - Wilson action S = beta sum_P (1 - Re Tr U_P / N);
+ *   - SU(2): Kennedy-Pendleton heat-bath, k = sqrt(det A), weight
+ *     exp(beta k a0);
+ *   - SU(3): Cabibbo-Marinari heat-bath over the SU(2) subgroups (0,1),(1,2),
+ *     (0,2), weight exp((2 beta / 3) k a0) per subgroup;
+ *   - microcanonical overrelaxation (SU(2) reflection, per SU(3) subgroup
+ *     R = (V^+)^2);
+ *   - reunitarization (SU(2) quaternion normalisation; SU(3) Gram-Schmidt of
+ *     rows 1, 2 and row 3 = conj(row1 x row2)), computed in FP64;
+ *   - background field: U(1) phase along lambda3 (sigma3 for SU(2)) on y-links,
+ *     B_y(x) = diag(e^{i phi}, e^{-i phi} [, 1]), phi = 2 pi n x / Ns^2, applied
+ *     as the effective link Ut = U B.  Updates act on Ut and store U = Ut B^+;
+ *   - random numbers: Philox-4x32-10 with key (seed_lo ^ lattice_id *
+ *     0x9E3779B9, seed_hi) and counter (site, sweep, mu | subgroup << 2 |
+ *     kind << 4, block), uniforms ((w >> 9) + 1/2) 2^-23.
+ *
+ * Conventions.
+ *   - mu = 0,1,2,3 is x,y,z,t; site s = x + Ns (y + Ns (z + Ns t)).
+ *   - Canonical host layout (get/set): FP64 [s][mu][row][col][re,im],
+ *     N*N complex numbers per link, x fastest.  It does not depend on the
+ *     device layout.
+ *   - Return value: QCD_OK (0) or a negative QCD_ERR_* code; no error is fatal
+ *     and qcd_last_error() gives a message for the calling thread.
+ *   - Ownership: the library owns the device memory it allocates, the caller
+ *     owns every host buffer it passes, the CUDA stream is borrowed.
+ *   - Ordering: every call is ordered on the lattice's stream.  Calls that
+ *     return host data (measure, get, counters) synchronize that stream.
+ *   - A handle is not thread-safe; distinct handles may be used concurrently.
+ */
+#ifndef QCD_H
+#define QCD_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define QCD_OK 0
+#define QCD_ERR_INVALID_ARG (-1)   /* bad group, odd/small extents, beta < 0 ... */
+#define QCD_ERR_OOM (-2)           /* device or host allocation failed          */
+#define QCD_ERR_CUDA (-3)          /* a CUDA call failed; see qcd_last_error()  */
+#define QCD_ERR_TIMEOUT (-4)       /* a bounded device wait ran out             */
+#define QCD_ERR_NOT_SUPPORTED (-5) /* valid but unsupported request            */
+
+/* Link storage. */
+#define QCD_FP64_PLAIN 0      /* SU(2): 4 FP64 reals; SU(3): 18 FP64 reals       */
+#define QCD_FP32_COMPRESSED 1 /* SU(2): 4 FP32 reals; SU(3): rows 1-2, 12 FP32
+                                 reals, row 3 rebuilt as conj(row1 x row2)      */
+/* Start. */
+#define QCD_COLD 0 /* every link the unit matrix                             */
+#define QCD_HOT 1  /* every link Haar-random: SU(2) Shoemake, SU(3) Mezzadri */
+/* Update kinds for qcd_phase. */
+#define QCD_HEATBATH 0
+#define QCD_OVERRELAX 1
+
+typedef struct qcd_lattice qcd_lattice;
+
+/* Create one lattice Ns^3 x Nt (finite temperature: sec. 4 singles out the
+ * time extent) and apply the start (sec. 5 "hot" initialisation).
+ *   out       receives the handle (NULL on failure).
+ *   group     2 or 3.
+ *   Ns, Nt    even, >= 2; Ns^3 Nt < 2^31.
+ *   beta      >= 0.
+ *   flux      flux quantum n of the background field (any integer, 0 = none).
+ *   precision QCD_FP64_PLAIN or QCD_FP32_COMPRESSED.
+ *   start     QCD_COLD or QCD_HOT.
+ *   seed      Philox key for the hot start and the default for qcd_sweep.
+ *   stream    cudaStream_t to order work on, or NULL for the default stream.
+ * Allocates the links and a few KB of reduction scratch on the current
+ * device.  NHIT defaults to 10 (sec. 5). */
+int qcd_lattice_create(qcd_lattice **out, int group, int Ns, int Nt,
+                       double beta, int flux, int precision, int start,
+                       uint64_t seed, void *stream);
+int qcd_lattice_destroy(qcd_lattice *lat);
+
+/* Cap on Kennedy-Pendleton tries per (link, subgroup); >= 1.  When every try
+ * is rejected the SU(2) link is kept and the SU(3) subgroup step is skipped
+ * (both leave the target distribution invariant); such events are counted. */
+int qcd_set_nhit(qcd_lattice *lat, int nhit);
+
+/* Sweep (sec. 3.3, sec. 5): n_heatbath times { one heat-bath pass; n_overrelax
+ * overrelaxation passes; FP64 reunitarization of every link }.  A pass visits
+ * the 8 checkerboard phases: parity even then odd, inside it mu = x,y,z,t.
+ * The sweep counter (Philox counter word 1) advances once per heat-bath pass.
+ * seed is the Philox key of this call (pass the create seed to continue one
+ * stream).  n_heatbath >= 0, n_overrelax >= 0. */
+int qcd_sweep(qcd_lattice *lat, int n_heatbath, int n_overrelax, uint64_t seed);
+
+/* One checkerboard phase (kind QCD_HEATBATH or QCD_OVERRELAX, parity 0/1,
+ * direction mu) at the current sweep counter; no reunitarization, no counter
+ * change.  For tests and sampled checks. */
+int qcd_phase(qcd_lattice *lat, int kind, int parity, int mu, uint64_t seed);
+/* FP64 reunitarization of every link. */
+int qcd_reunitarize(qcd_lattice *lat);
+
+/* Measurements on the effective links (sec. 1, sec. 5), FP64 sums:
+ *   plaquette[3] = {P, P_s, P_t}: (1/N) Re Tr of the plaquette averaged over
+ *     all 6V plaquettes, the 3V spatial ones (mu,nu < t) and the 3V temporal;
+ *   polyakov[2] = {Re L, Im L}: (1/N) Tr of the ordered product of t-links
+ *     t = 0..Nt-1, averaged over the Ns^3 spatial sites.
+ * Either pointer may be NULL.  Host pointers; synchronizes the stream. */
+int qcd_measure(qcd_lattice *lat, double *plaquette, double *polyakov);
+/* The same plaquettes on the bare links U (they depend on the field). */
+int qcd_measure_bare(qcd_lattice *lat, double *plaquette);
+
+/* Links in the canonical FP64 host layout (4 V N^2 complex numbers).
+ * set_links rounds to the storage (FP32-12 keeps rows 1-2; SU(2) keeps the
+ * SU(2)-projection q0 + i q.sigma of each 2x2 matrix). */
+int qcd_get_links(qcd_lattice *lat, double *host_out);
+int qcd_set_links(qcd_lattice *lat, const double *host_in);
+
+/* Raw device storage to and from a host buffer of qcd_link_bytes() bytes
+ * (pinned memory gives full copy speed).  Used for checkpoints and for
+ * end-to-end runs that stage configurations on the host. */
+int qcd_link_bytes(const qcd_lattice *lat, size_t *bytes);
+int qcd_copy_links_in(qcd_lattice *lat, const void *host_in, size_t bytes);
+int qcd_copy_links_out(qcd_lattice *lat, void *host_out, size_t bytes);
+
+/* Sweep counter (heat-bath passes since the start) and NHIT-exhaustion
+ * counter. */
+int qcd_get_sweep(qcd_lattice *lat, uint32_t *sweep);
+int qcd_set_sweep(qcd_lattice *lat, uint32_t sweep);
+int qcd_get_exhausted(qcd_lattice *lat, unsigned long long *count);
+
+/* Launch shape: threads per block of the phase kernels (0 = autotune on the
+ * next sweep; otherwise a multiple of 32 in [32, 1024]). */
+int qcd_set_block(qcd_lattice *lat, int threads);
+int qcd_get_block(const qcd_lattice *lat, int *threads);
+
+/* Live kernel timing (the paper's optional run-time profiling of kernels,
+ * sec. 3.2).  When enabled, CUDA events are recorded on the lattice's stream
+ * around every kernel the sweep and the measurements launch (inside the
+ * captured sweep graph), and their durations are accumulated per category:
+ *   QCD_PROF_HEATBATH  heat-bath phase kernels
+ *   QCD_PROF_OVERRELAX overrelaxation phase kernels
+ *   QCD_PROF_REUNIT    reunitarization kernel
+ *   QCD_PROF_MEASURE   measurement kernels (block partials + final sum)
+ * Enabling or disabling resets the totals.  While enabled, each sweep waits
+ * for its own completion before the next is queued.  qcd_get_profile fills
+ * ms[QCD_PROF_N] (total milliseconds) and launches[QCD_PROF_N]; it
+ * synchronizes the stream. */
+#define QCD_PROF_HEATBATH 0
+#define QCD_PROF_OVERRELAX 1
+#define QCD_PROF_REUNIT 2
+#define QCD_PROF_MEASURE 3
+#define QCD_PROF_N 4
+int qcd_set_profiling(qcd_lattice *lat, int enable);
+int qcd_get_profile(qcd_lattice *lat, double *ms, unsigned long long *launches);
+
+/* Message of the last failed call on this thread ("" if none). */
+const char *qcd_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -60,6 +60,8 @@ def lib() -> ctypes.CDLL:
         L.oracle_create.restype = vp
         L.oracle_destroy.argtypes = [vp]
         L.oracle_set_threads.argtypes = [i]
+        L.oracle_get_threads.argtypes = []
+        L.oracle_get_threads.restype = i
         L.oracle_cold_start.argtypes = [vp]
         L.oracle_hot_start.argtypes = [vp, u64]
         L.oracle_sweep.argtypes = [vp, i, i, u64]
@@ -93,6 +95,10 @@ def _dptr(a: np.ndarray):
 
 def set_threads(n: int) -> None:
     lib().oracle_set_threads(int(n))
+
+
+def get_threads() -> int:
+    return lib().oracle_get_threads()
 
 
 def philox4x32_10(ctr, key):

@@ -358,37 +358,40 @@ static mat staple(const oracle_lattice *L, long s, int mu)
 /* Random SU(2) elements                                                     */
 /* ------------------------------------------------------------------------ */
 
-/* Kennedy-Pendleton draw of a0 in [-1, 1] with density proportional to
- * sqrt(1 - a0^2) exp(alpha a0), alpha > 0.  Try t reads block t of the stream
- * as u1..u4; delta = (-ln u2 - ln u1 cos^2(2 pi u3)) / alpha is a
- * Gamma(3/2, 1/alpha) variate, accepted when u4^2 <= 1 - delta/2, giving
- * a0 = 1 - delta.  Returns the number of tries used, 0 if all nhit failed. */
-static int kp_draw(double alpha, int nhit, const stream *st, double *a0)
+/* Kennedy-Pendleton draw of a0 = 1 - delta in [-1, 1] with density
+ * proportional to sqrt(1 - a0^2) exp(alpha a0), alpha > 0.  Try t reads block
+ * t of the stream as u1..u4; delta = (-ln u2 - ln u1 cos^2(2 pi u3)) / alpha is
+ * a Gamma(3/2, 1/alpha) variate, accepted when u4^2 <= 1 - delta/2.  Returns
+ * the number of tries used (delta in *delta), 0 if all nhit failed. */
+static int kp_draw(double alpha, int nhit, const stream *st, double *delta)
 {
     for (int t = 0; t < nhit; ++t) {
         double u[4];
         stream_uniforms(st, (uint32_t)t, u);
         double c = cos(2.0 * M_PI * u[2]);
-        double delta = (-log(u[1]) - log(u[0]) * c * c) / alpha;
-        if (u[3] * u[3] <= 1.0 - 0.5 * delta) {
-            *a0 = 1.0 - delta;
+        double d = (-log(u[1]) - log(u[0]) * c * c) / alpha;
+        if (u[3] * u[3] <= 1.0 - 0.5 * d) {
+            *delta = d;
             return t + 1;
         }
     }
     return 0;
 }
 
-/* Unit quaternion with real part a0 and a direction uniform on S^2, read from
- * block 0 of the direction stream: cos(theta) = 2 u1 - 1, phi = 2 pi u2. */
-static void su2_with_a0(double a0, const stream *dir, double x[4])
+/* Unit quaternion with real part a0 = 1 - delta and a direction uniform on
+ * S^2, read from block 0 of the direction stream: cos(theta) = 2 u1 - 1,
+ * phi = 2 pi u2.  The moduli are written without cancellation:
+ * sqrt(1 - a0^2) = sqrt(delta (2 - delta)) and
+ * sin(theta) = sqrt(1 - cos^2(theta)) = 2 sqrt(u1 (1 - u1)). */
+static void su2_with_delta(double delta, const stream *dir, double x[4])
 {
     double u[4];
     stream_uniforms(dir, 0, u);
     double ct = 2.0 * u[0] - 1.0;
-    double st = sqrt(1.0 - ct * ct);
+    double st = 2.0 * sqrt(u[0] * (1.0 - u[0]));
     double ph = 2.0 * M_PI * u[1];
-    double r = sqrt(1.0 - a0 * a0);
-    x[0] = a0;
+    double r = sqrt(delta * (2.0 - delta));
+    x[0] = 1.0 - delta;
     x[1] = r * st * cos(ph);
     x[2] = r * st * sin(ph);
     x[3] = r * ct;
@@ -461,12 +464,12 @@ static int heatbath_su2(const oracle_lattice *L, uint64_t seed, long s, int mu,
         ut_new = quat_to_mat(x);
     } else {
         stream tries = lattice_stream(L, seed, L->sweep, s, mu, 0, KIND_TRY);
-        double a0;
-        if (!kp_draw(alpha, L->nhit, &tries, &a0)) {
+        double delta;
+        if (!kp_draw(alpha, L->nhit, &tries, &delta)) {
             *out = get_link(L, s, mu);
             return 1;
         }
-        su2_with_a0(a0, &dir, x);
+        su2_with_delta(delta, &dir, x);
         mat xm = quat_to_mat(x);
         mat v = a;
         for (int i = 0; i < 2; ++i)
@@ -528,12 +531,12 @@ static int heatbath_su3(const oracle_lattice *L, uint64_t seed, long s, int mu,
             r = quat_to_mat(x);
         } else {
             stream tries = lattice_stream(L, seed, L->sweep, s, mu, sub, KIND_TRY);
-            double a0;
-            if (!kp_draw(alpha, L->nhit, &tries, &a0)) {
+            double delta;
+            if (!kp_draw(alpha, L->nhit, &tries, &delta)) {
                 ++exhausted;
                 continue;
             }
-            su2_with_a0(a0, &dir, x);
+            su2_with_delta(delta, &dir, x);
             double vq[4] = { q[0] / k, q[1] / k, q[2] / k, q[3] / k };
             mat xm = quat_to_mat(x), v = quat_to_mat(vq), vd = mat_dag(2, &v);
             r = mat_mul(2, &xm, &vd);
@@ -649,6 +652,15 @@ void oracle_set_threads(int n)
     if (n > 0) omp_set_num_threads(n);
 #else
     (void)n;
+#endif
+}
+
+int oracle_get_threads(void)
+{
+#ifdef _OPENMP
+    return omp_get_max_threads();
+#else
+    return 1;
 #endif
 }
 
@@ -850,9 +862,9 @@ void oracle_kp_samples(double alpha, int nhit, uint64_t seed, long n,
 #pragma omp parallel for schedule(static)
     for (long i = 0; i < n; ++i) {
         stream st = plain_stream(seed, (uint32_t)i, 0, KIND_TRY << 4);
-        double a = 0.0;
-        tries[i] = kp_draw(alpha, nhit, &st, &a);
-        a0[i] = a;
+        double d = 0.0;
+        tries[i] = kp_draw(alpha, nhit, &st, &d);
+        a0[i] = tries[i] ? 1.0 - d : 0.0;
     }
 }
 
@@ -868,12 +880,12 @@ void oracle_su2_samples(double alpha, int nhit, uint64_t seed, long n,
             continue;
         }
         stream st = plain_stream(seed, (uint32_t)i, 0, KIND_TRY << 4);
-        double a0;
-        if (!kp_draw(alpha, nhit, &st, &a0)) {
+        double delta;
+        if (!kp_draw(alpha, nhit, &st, &delta)) {
             x[0] = x[1] = x[2] = x[3] = 0.0;
             continue;
         }
-        su2_with_a0(a0, &dir, x);
+        su2_with_delta(delta, &dir, x);
     }
 }
 

@@ -47,6 +47,7 @@ oracle_lattice *oracle_create(int N, int Ns, int Nt, double beta, int flux,
                               int nhit, uint32_t lattice_id);
 void oracle_destroy(oracle_lattice *L);
 void oracle_set_threads(int n);
+int oracle_get_threads(void);
 
 void oracle_cold_start(oracle_lattice *L);
 void oracle_hot_start(oracle_lattice *L, uint64_t seed);

@@ -1,0 +1,286 @@
+"""Python binding of libqcdgb300 (include/qcd.h): the checkerboard Monte Carlo
+sweep of SU(2)/SU(3) Wilson lattice gauge theory at finite temperature in a
+constant Abelian background field, on one GB300.
+
+Argument marshalling only: every step of the sweep and of the measurements
+runs in the library's CUDA kernels.  There is no CPU fallback; when the
+compiled library is missing every call raises.  PyTorch supplies the CUDA
+stream (``torch.cuda.current_stream()`` unless one is given).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libqcdgb300.so")
+
+QCD_OK = 0
+QCD_ERR_INVALID_ARG = -1
+QCD_ERR_OOM = -2
+QCD_ERR_CUDA = -3
+QCD_ERR_TIMEOUT = -4
+QCD_ERR_NOT_SUPPORTED = -5
+QCD_FP64_PLAIN = 0
+QCD_FP32_COMPRESSED = 1
+QCD_COLD = 0
+QCD_HOT = 1
+QCD_HEATBATH = 0
+QCD_OVERRELAX = 1
+
+# Every symbol include/qcd.h declares, with ctypes (restype, argtypes).
+_vp, _i, _d, _u32, _u64, _sz = (ctypes.c_void_p, ctypes.c_int, ctypes.c_double,
+                                ctypes.c_uint32, ctypes.c_uint64, ctypes.c_size_t)
+_P = ctypes.POINTER
+SIGNATURES = {
+    "qcd_lattice_create": (_i, [_P(_vp), _i, _i, _i, _d, _i, _i, _i, _u64, _vp]),
+    "qcd_lattice_destroy": (_i, [_vp]),
+    "qcd_set_nhit": (_i, [_vp, _i]),
+    "qcd_sweep": (_i, [_vp, _i, _i, _u64]),
+    "qcd_phase": (_i, [_vp, _i, _i, _i, _u64]),
+    "qcd_reunitarize": (_i, [_vp]),
+    "qcd_measure": (_i, [_vp, _P(_d), _P(_d)]),
+    "qcd_measure_bare": (_i, [_vp, _P(_d)]),
+    "qcd_get_links": (_i, [_vp, _P(_d)]),
+    "qcd_set_links": (_i, [_vp, _P(_d)]),
+    "qcd_link_bytes": (_i, [_vp, _P(_sz)]),
+    "qcd_copy_links_in": (_i, [_vp, _vp, _sz]),
+    "qcd_copy_links_out": (_i, [_vp, _vp, _sz]),
+    "qcd_get_sweep": (_i, [_vp, _P(_u32)]),
+    "qcd_set_sweep": (_i, [_vp, _u32]),
+    "qcd_get_exhausted": (_i, [_vp, _P(ctypes.c_ulonglong)]),
+    "qcd_set_block": (_i, [_vp, _i]),
+    "qcd_get_block": (_i, [_vp, _P(_i)]),
+    "qcd_set_profiling": (_i, [_vp, _i]),
+    "qcd_get_profile": (_i, [_vp, _P(_d), _P(ctypes.c_ulonglong)]),
+    "qcd_last_error": (ctypes.c_char_p, []),
+}
+QCD_PROF_HEATBATH, QCD_PROF_OVERRELAX, QCD_PROF_REUNIT, QCD_PROF_MEASURE = 0, 1, 2, 3
+QCD_PROF_N = 4
+
+
+class QcdError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__("qcd error %d: %s" % (code, msg))
+        self.code = code
+
+
+_lib = None
+
+
+def lib() -> ctypes.CDLL:
+    """The loaded CUDA library; raises if it has not been built."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError("libqcdgb300.so is not built (run __graft_entry__.build()); "
+                               "there is no CPU fallback")
+        L = ctypes.CDLL(LIB_PATH)
+        for name, (res, args) in SIGNATURES.items():
+            fn = getattr(L, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = L
+    return _lib
+
+
+def _check(rc: int) -> None:
+    if rc != QCD_OK:
+        raise QcdError(rc, lib().qcd_last_error().decode())
+
+
+def _stream_handle(stream) -> int:
+    if stream is None:
+        import torch
+        return int(torch.cuda.current_stream().cuda_stream)
+    if isinstance(stream, int):
+        return stream
+    return int(stream.cuda_stream)
+
+
+def _dptr(a: np.ndarray):
+    assert a.dtype == np.float64 and a.flags["C_CONTIGUOUS"]
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+# ---- the C ABI, one Python function per entry point ------------------------
+
+def qcd_lattice_create(group, Ns, Nt, beta, flux=0, precision=QCD_FP32_COMPRESSED,
+                       start=QCD_HOT, seed=1, stream=None) -> ctypes.c_void_p:
+    h = ctypes.c_void_p()
+    _check(lib().qcd_lattice_create(ctypes.byref(h), group, Ns, Nt, beta, flux, precision,
+                                    start, seed, _stream_handle(stream)))
+    return h
+
+
+def qcd_lattice_destroy(h) -> None:
+    _check(lib().qcd_lattice_destroy(h))
+
+
+def qcd_set_nhit(h, nhit: int) -> None:
+    _check(lib().qcd_set_nhit(h, nhit))
+
+
+def qcd_sweep(h, n_heatbath: int, n_overrelax: int, seed: int) -> None:
+    _check(lib().qcd_sweep(h, n_heatbath, n_overrelax, seed))
+
+
+def qcd_phase(h, kind: int, parity: int, mu: int, seed: int) -> None:
+    _check(lib().qcd_phase(h, kind, parity, mu, seed))
+
+
+def qcd_reunitarize(h) -> None:
+    _check(lib().qcd_reunitarize(h))
+
+
+def qcd_measure(h):
+    p = (ctypes.c_double * 3)()
+    l = (ctypes.c_double * 2)()
+    _check(lib().qcd_measure(h, p, l))
+    return list(p), list(l)
+
+
+def qcd_measure_bare(h):
+    p = (ctypes.c_double * 3)()
+    _check(lib().qcd_measure_bare(h, p))
+    return list(p)
+
+
+def qcd_get_links(h, V: int, N: int) -> np.ndarray:
+    out = np.empty((V, 4, N, N, 2), np.float64)
+    _check(lib().qcd_get_links(h, _dptr(out)))
+    return out[..., 0] + 1j * out[..., 1]
+
+
+def qcd_set_links(h, links) -> None:
+    a = np.asarray(links)
+    if np.iscomplexobj(a):
+        a = np.stack([a.real, a.imag], axis=-1)
+    a = np.ascontiguousarray(a, dtype=np.float64)
+    _check(lib().qcd_set_links(h, _dptr(a)))
+
+
+def qcd_link_bytes(h) -> int:
+    n = ctypes.c_size_t()
+    _check(lib().qcd_link_bytes(h, ctypes.byref(n)))
+    return n.value
+
+
+def qcd_copy_links_in(h, host_ptr: int, nbytes: int) -> None:
+    _check(lib().qcd_copy_links_in(h, host_ptr, nbytes))
+
+
+def qcd_copy_links_out(h, host_ptr: int, nbytes: int) -> None:
+    _check(lib().qcd_copy_links_out(h, host_ptr, nbytes))
+
+
+def qcd_get_sweep(h) -> int:
+    v = ctypes.c_uint32()
+    _check(lib().qcd_get_sweep(h, ctypes.byref(v)))
+    return v.value
+
+
+def qcd_set_sweep(h, sweep: int) -> None:
+    _check(lib().qcd_set_sweep(h, sweep))
+
+
+def qcd_get_exhausted(h) -> int:
+    v = ctypes.c_ulonglong()
+    _check(lib().qcd_get_exhausted(h, ctypes.byref(v)))
+    return v.value
+
+
+def qcd_set_block(h, threads: int) -> None:
+    _check(lib().qcd_set_block(h, threads))
+
+
+def qcd_get_block(h) -> int:
+    v = ctypes.c_int()
+    _check(lib().qcd_get_block(h, ctypes.byref(v)))
+    return v.value
+
+
+def qcd_set_profiling(h, enable: bool) -> None:
+    _check(lib().qcd_set_profiling(h, int(bool(enable))))
+
+
+def qcd_get_profile(h):
+    """(ms[QCD_PROF_N], launches[QCD_PROF_N]) accumulated since profiling was
+    enabled: heat-bath, overrelaxation, reunitarization, measurement."""
+    ms = (ctypes.c_double * QCD_PROF_N)()
+    n = (ctypes.c_ulonglong * QCD_PROF_N)()
+    _check(lib().qcd_get_profile(h, ms, n))
+    return list(ms), list(n)
+
+
+def qcd_last_error() -> str:
+    return lib().qcd_last_error().decode()
+
+
+class Lattice:
+    """Owning wrapper around one ``qcd_lattice`` handle."""
+
+    def __init__(self, group, Ns, Nt, beta, flux=0, precision=QCD_FP32_COMPRESSED,
+                 start=QCD_HOT, seed=1, stream=None, nhit=10):
+        self.group, self.Ns, self.Nt = group, Ns, Nt
+        self.V = Ns ** 3 * Nt
+        self.beta, self.flux, self.precision, self.seed = beta, flux, precision, seed
+        self.h = qcd_lattice_create(group, Ns, Nt, beta, flux, precision, start, seed, stream)
+        if nhit != 10:
+            qcd_set_nhit(self.h, nhit)
+
+    def close(self):
+        if self.h:
+            qcd_lattice_destroy(self.h)
+            self.h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def sweep(self, n_hb=1, n_or=1, seed=None):
+        qcd_sweep(self.h, n_hb, n_or, self.seed if seed is None else seed)
+
+    def phase(self, kind, parity, mu, seed=None):
+        qcd_phase(self.h, kind, parity, mu, self.seed if seed is None else seed)
+
+    def reunitarize(self):
+        qcd_reunitarize(self.h)
+
+    def measure(self):
+        return qcd_measure(self.h)
+
+    def measure_bare(self):
+        return qcd_measure_bare(self.h)
+
+    def get_links(self):
+        return qcd_get_links(self.h, self.V, self.group)
+
+    def set_links(self, links):
+        qcd_set_links(self.h, links)
+
+    @property
+    def sweep_counter(self):
+        return qcd_get_sweep(self.h)
+
+    @sweep_counter.setter
+    def sweep_counter(self, v):
+        qcd_set_sweep(self.h, v)
+
+    @property
+    def exhausted(self):
+        return qcd_get_exhausted(self.h)
+
+    @property
+    def link_bytes(self):
+        return qcd_link_bytes(self.h)

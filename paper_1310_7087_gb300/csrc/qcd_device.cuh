@@ -1,0 +1,341 @@
+// qcd_device.cuh -- device-side building blocks of the gauge sweep:
+// complex numbers, SU(2) as unit quaternions, SU(3) as 3x3 complex matrices,
+// Philox-4x32-10, lattice geometry on the even/odd layout, link storage.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "qcd_internal.h"
+
+namespace qcd {
+
+// ---------------------------------------------------------------------------
+// Complex arithmetic
+// ---------------------------------------------------------------------------
+template <typename R>
+struct Cx {
+  R re, im;
+};
+
+template <typename R>
+__device__ __forceinline__ Cx<R> cx(R re, R im) { return {re, im}; }
+template <typename R>
+__device__ __forceinline__ Cx<R> operator+(Cx<R> a, Cx<R> b) { return {a.re + b.re, a.im + b.im}; }
+template <typename R>
+__device__ __forceinline__ Cx<R> operator-(Cx<R> a, Cx<R> b) { return {a.re - b.re, a.im - b.im}; }
+template <typename R>
+__device__ __forceinline__ Cx<R> operator*(Cx<R> a, Cx<R> b) {
+  return {a.re * b.re - a.im * b.im, a.re * b.im + a.im * b.re};
+}
+template <typename R>
+__device__ __forceinline__ Cx<R> conj(Cx<R> a) { return {a.re, -a.im}; }
+template <typename R>
+__device__ __forceinline__ Cx<R> scale(Cx<R> a, R s) { return {a.re * s, a.im * s}; }
+// acc + a * b
+template <typename R>
+__device__ __forceinline__ Cx<R> cfma(Cx<R> a, Cx<R> b, Cx<R> acc) {
+  return {fma(a.re, b.re, fma(-a.im, b.im, acc.re)), fma(a.re, b.im, fma(a.im, b.re, acc.im))};
+}
+// acc + a * conj(b)
+template <typename R>
+__device__ __forceinline__ Cx<R> cfma_nc(Cx<R> a, Cx<R> b, Cx<R> acc) {
+  return {fma(a.re, b.re, fma(a.im, b.im, acc.re)), fma(a.im, b.re, fma(-a.re, b.im, acc.im))};
+}
+// acc + conj(a) * b
+template <typename R>
+__device__ __forceinline__ Cx<R> cfma_cn(Cx<R> a, Cx<R> b, Cx<R> acc) {
+  return {fma(a.re, b.re, fma(a.im, b.im, acc.re)), fma(a.re, b.im, fma(-a.im, b.re, acc.im))};
+}
+
+// ---------------------------------------------------------------------------
+// SU(2) as unit quaternions q0 + i (q1 s1 + q2 s2 + q3 s3), i.e. the matrix
+// [[q0 + i q3, q2 + i q1], [-q2 + i q1, q0 - i q3]].  Real multiples of SU(2)
+// (staple sums) use the same type.
+// ---------------------------------------------------------------------------
+template <typename R>
+struct Quat {
+  R q0, q1, q2, q3;
+};
+
+// Matrix product a b:  (a0 b0 - a.b,  a0 b + b0 a - a x b)
+template <typename R>
+__device__ __forceinline__ Quat<R> qmul(const Quat<R>& a, const Quat<R>& b) {
+  Quat<R> c;
+  c.q0 = a.q0 * b.q0 - a.q1 * b.q1 - a.q2 * b.q2 - a.q3 * b.q3;
+  c.q1 = a.q0 * b.q1 + b.q0 * a.q1 - (a.q2 * b.q3 - a.q3 * b.q2);
+  c.q2 = a.q0 * b.q2 + b.q0 * a.q2 - (a.q3 * b.q1 - a.q1 * b.q3);
+  c.q3 = a.q0 * b.q3 + b.q0 * a.q3 - (a.q1 * b.q2 - a.q2 * b.q1);
+  return c;
+}
+template <typename R>
+__device__ __forceinline__ Quat<R> qdag(const Quat<R>& a) { return {a.q0, -a.q1, -a.q2, -a.q3}; }
+template <typename R>
+__device__ __forceinline__ Quat<R> qadd(const Quat<R>& a, const Quat<R>& b) {
+  return {a.q0 + b.q0, a.q1 + b.q1, a.q2 + b.q2, a.q3 + b.q3};
+}
+template <typename R>
+__device__ __forceinline__ Quat<R> qscale(const Quat<R>& a, R s) { return {a.q0 * s, a.q1 * s, a.q2 * s, a.q3 * s}; }
+template <typename R>
+__device__ __forceinline__ R qnorm2(const Quat<R>& a) { return a.q0 * a.q0 + a.q1 * a.q1 + a.q2 * a.q2 + a.q3 * a.q3; }
+
+// ---------------------------------------------------------------------------
+// SU(3) as full 3x3 complex matrices in registers.
+// ---------------------------------------------------------------------------
+template <typename R>
+struct M3 {
+  Cx<R> e[3][3];
+};
+
+template <typename R>
+__device__ __forceinline__ void m3_zero(M3<R>& m) {
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int j = 0; j < 3; ++j) m.e[i][j] = {R(0), R(0)};
+}
+
+// a b
+template <typename R>
+__device__ __forceinline__ M3<R> m3_mul(const M3<R>& a, const M3<R>& b) {
+  M3<R> c;
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+      Cx<R> acc = a.e[i][0] * b.e[0][j];
+      acc = cfma(a.e[i][1], b.e[1][j], acc);
+      acc = cfma(a.e[i][2], b.e[2][j], acc);
+      c.e[i][j] = acc;
+    }
+  return c;
+}
+// a b^+
+template <typename R>
+__device__ __forceinline__ M3<R> m3_mul_nd(const M3<R>& a, const M3<R>& b) {
+  M3<R> c;
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+      Cx<R> acc = {R(0), R(0)};
+#pragma unroll
+      for (int k = 0; k < 3; ++k) acc = cfma_nc(a.e[i][k], b.e[j][k], acc);
+      c.e[i][j] = acc;
+    }
+  return c;
+}
+// acc += a^+ b
+template <typename R>
+__device__ __forceinline__ void m3_acc_dn(M3<R>& acc, const M3<R>& a, const M3<R>& b) {
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+      Cx<R> s = acc.e[i][j];
+#pragma unroll
+      for (int k = 0; k < 3; ++k) s = cfma_cn(a.e[k][i], b.e[k][j], s);
+      acc.e[i][j] = s;
+    }
+}
+// acc += a b^+
+template <typename R>
+__device__ __forceinline__ void m3_acc_nd(M3<R>& acc, const M3<R>& a, const M3<R>& b) {
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+      Cx<R> s = acc.e[i][j];
+#pragma unroll
+      for (int k = 0; k < 3; ++k) s = cfma_nc(a.e[i][k], b.e[j][k], s);
+      acc.e[i][j] = s;
+    }
+}
+template <typename R>
+__device__ __forceinline__ M3<R> m3_dag(const M3<R>& a) {
+  M3<R> c;
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int j = 0; j < 3; ++j) c.e[i][j] = conj(a.e[j][i]);
+  return c;
+}
+template <typename R>
+__device__ __forceinline__ R m3_retrace(const M3<R>& a) {
+  return a.e[0][0].re + a.e[1][1].re + a.e[2][2].re;
+}
+// Re Tr(a b) without forming the product.
+template <typename R>
+__device__ __forceinline__ R m3_retrace_mul(const M3<R>& a, const M3<R>& b) {
+  R s = R(0);
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int k = 0; k < 3; ++k) s = fma(a.e[i][k].re, b.e[k][i].re, fma(-a.e[i][k].im, b.e[k][i].im, s));
+  return s;
+}
+// row 2 = conj(row0 x row1): the third row of an SU(3) matrix.
+template <typename R>
+__device__ __forceinline__ void m3_rebuild_row2(M3<R>& m) {
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    const int c1 = (c + 1) % 3, c2 = (c + 2) % 3;
+    Cx<R> v = m.e[0][c1] * m.e[1][c2] - m.e[0][c2] * m.e[1][c1];
+    m.e[2][c] = conj(v);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Philox-4x32-10 (Salmon et al., SC11): 10 rounds, two 32x32->64 multiplies
+// per round, key bumped by the Weyl constants between rounds.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint32_t k0, uint32_t k1) {
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    if (r > 0) {
+      k0 += 0x9E3779B9u;
+      k1 += 0xBB67AE85u;
+    }
+    const uint32_t lo0 = 0xD2511F53u * c.x, hi0 = __umulhi(0xD2511F53u, c.x);
+    const uint32_t lo1 = 0xCD9E8D57u * c.z, hi1 = __umulhi(0xCD9E8D57u, c.z);
+    c = make_uint4(hi1 ^ c.y ^ k0, lo1, hi0 ^ c.w ^ k1, lo0);
+  }
+  return c;
+}
+
+// ((w >> 9) + 1/2) 2^-23: a uniform in (0,1), exact in FP32 and FP64.
+template <typename R>
+__device__ __forceinline__ R u01(uint32_t w) {
+  return (R(w >> 9) + R(0.5)) * R(1.1920928955078125e-07);
+}
+
+enum : uint32_t { KIND_TRY = 0u, KIND_DIR = 1u, KIND_START = 2u };
+constexpr uint32_t START_SWEEP_WORD = 0xFFFFFFFFu;
+
+struct Stream {
+  uint32_t k0, k1, c0, c1, c2;
+  template <typename R>
+  __device__ __forceinline__ void uniforms(uint32_t block, R u[4]) const {
+    uint4 w = philox4x32_10(make_uint4(c0, c1, c2, block), k0, k1);
+    u[0] = u01<R>(w.x);
+    u[1] = u01<R>(w.y);
+    u[2] = u01<R>(w.z);
+    u[3] = u01<R>(w.w);
+  }
+};
+
+__device__ __forceinline__ Stream make_stream(uint32_t k0, uint32_t k1, uint32_t site, uint32_t sweep, int mu,
+                                              int sub, uint32_t kind) {
+  return Stream{k0, k1, site, sweep, uint32_t(mu) | (uint32_t(sub) << 2) | (kind << 4)};
+}
+
+// Transcendentals in the working precision.
+__device__ __forceinline__ float q_log(float x) { return logf(x); }
+__device__ __forceinline__ double q_log(double x) { return log(x); }
+__device__ __forceinline__ float q_sqrt(float x) { return sqrtf(x); }
+__device__ __forceinline__ double q_sqrt(double x) { return sqrt(x); }
+__device__ __forceinline__ float q_cospi(float x) { return cospif(x); }
+__device__ __forceinline__ double q_cospi(double x) { return cospi(x); }
+__device__ __forceinline__ void q_sincospi(float x, float* s, float* c) { sincospif(x, s, c); }
+__device__ __forceinline__ void q_sincospi(double x, double* s, double* c) { sincospi(x, s, c); }
+
+// Kennedy-Pendleton draw with density ~ sqrt(1 - a0^2) exp(alpha a0),
+// returned as delta = 1 - a0: try t uses block t,
+// delta = (-ln u2 - ln u1 cos^2(2 pi u3)) / alpha, accepted when
+// u4^2 <= 1 - delta / 2.  Returns false when all nhit tries fail.
+template <typename R>
+__device__ __forceinline__ bool kp_draw(R alpha, int nhit, const Stream& st, R& delta) {
+  const R inv_alpha = R(1) / alpha;
+  for (int t = 0; t < nhit; ++t) {
+    R u[4];
+    st.uniforms<R>(uint32_t(t), u);
+    const R c = q_cospi(R(2) * u[2]);
+    const R d = (-q_log(u[1]) - q_log(u[0]) * c * c) * inv_alpha;
+    if (u[3] * u[3] <= R(1) - R(0.5) * d) {
+      delta = d;
+      return true;
+    }
+  }
+  return false;
+}
+
+// Unit quaternion with real part a0 = 1 - delta and a direction uniform on
+// S^2 from block 0 of the direction stream: cos(theta) = 2 u1 - 1,
+// phi = 2 pi u2.  The moduli use the cancellation-free forms
+// sqrt(1 - a0^2) = sqrt(delta (2 - delta)) and
+// sin(theta) = sqrt(1 - (2 u1 - 1)^2) = 2 sqrt(u1 (1 - u1)).
+template <typename R>
+__device__ __forceinline__ Quat<R> su2_with_delta(R delta, const Stream& dir) {
+  R u[4];
+  dir.uniforms<R>(0u, u);
+  const R ct = R(2) * u[0] - R(1);
+  const R st = R(2) * q_sqrt(u[0] * (R(1) - u[0]));
+  R sp, cp;
+  q_sincospi(R(2) * u[1], &sp, &cp);
+  const R r = q_sqrt(delta * (R(2) - delta));
+  return {R(1) - delta, r * st * cp, r * st * sp, r * ct};
+}
+
+// Haar-random unit quaternion (Shoemake) from one block.
+template <typename R>
+__device__ __forceinline__ Quat<R> su2_haar(const Stream& st, uint32_t block) {
+  R u[4];
+  st.uniforms<R>(block, u);
+  const R r1 = q_sqrt(R(1) - u[0]), r2 = q_sqrt(u[0]);
+  R s1, c1, s2, c2;
+  q_sincospi(R(2) * u[1], &s1, &c1);
+  q_sincospi(R(2) * u[2], &s2, &c2);
+  return {r1 * s1, r1 * c1, r2 * s2, r2 * c2};
+}
+
+// ---------------------------------------------------------------------------
+// Geometry.  Site s = x + Ns (y + Ns (z + Ns t)); the even/odd layout keeps
+// h = s >> 1 inside each parity (Ns even, so s and s^1 share y,z,t and differ
+// in parity).
+// ---------------------------------------------------------------------------
+using Geom = GeomH;  // Ns, Nt, Vh = sites per parity, plane = vectors per plane
+
+struct Site {
+  int x, y, z, t;
+};
+
+__device__ __forceinline__ Site site_of(const Geom& g, int parity, int h) {
+  int r = 2 * h;
+  Site c;
+  const int x0 = r % g.Ns;
+  r /= g.Ns;
+  c.y = r % g.Ns;
+  r /= g.Ns;
+  c.z = r % g.Ns;
+  c.t = r / g.Ns;
+  c.x = x0 + ((parity + c.y + c.z + c.t) & 1);
+  return c;
+}
+__device__ __forceinline__ int lex(const Geom& g, const Site& c) {
+  return c.x + g.Ns * (c.y + g.Ns * (c.z + g.Ns * c.t));
+}
+__device__ __forceinline__ int parity_of(const Site& c) { return (c.x + c.y + c.z + c.t) & 1; }
+__device__ __forceinline__ Site step(const Geom& g, Site c, int mu, int d) {
+  // d = +1 or -1, periodic
+  if (mu == 0) {
+    c.x += d;
+    c.x = c.x < 0 ? g.Ns - 1 : (c.x >= g.Ns ? 0 : c.x);
+  } else if (mu == 1) {
+    c.y += d;
+    c.y = c.y < 0 ? g.Ns - 1 : (c.y >= g.Ns ? 0 : c.y);
+  } else if (mu == 2) {
+    c.z += d;
+    c.z = c.z < 0 ? g.Ns - 1 : (c.z >= g.Ns ? 0 : c.z);
+  } else {
+    c.t += d;
+    c.t = c.t < 0 ? g.Nt - 1 : (c.t >= g.Nt ? 0 : c.t);
+  }
+  return c;
+}
+
+// Vector index of component comp of link (mu, parity, h).
+__device__ __forceinline__ int64_t vidx(const Geom& g, int comp, int mu, int parity, int h) {
+  return (int64_t(comp * 4 + mu) * 2 + parity) * g.plane + h;
+}
+
+}  // namespace qcd

@@ -1,0 +1,63 @@
+// qcd_internal.h -- interface between the host library (qcd_api.cu) and the
+// per-storage kernel translation units.  Not part of the public ABI.
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace qcd {
+
+struct GeomH {
+  int Ns, Nt;
+  int Vh;
+  int64_t plane;
+};
+
+// Everything a kernel launch needs for one lattice.  Device pointers only.
+struct Ctx {
+  void* links;
+  GeomH g;
+  double beta;
+  uint32_t k0, k1;              // Philox key of this call
+  const uint32_t* sweep;        // device sweep counter (Philox counter word 1)
+  uint32_t* sweep_rw;           // same counter, for the end-of-sweep advance
+  int nhit;
+  int flux;                     // 0: no background field
+  const double2* phase64;       // per x: (cos phi, sin phi), phi = 2 pi n x / Ns^2
+  const float2* phase32;
+  unsigned long long* exhausted;
+  double* partials;             // measurement scratch, measure_partials() doubles
+  double* meas_out;             // 5 doubles: P, P_s, P_t, Re L, Im L
+};
+
+constexpr int MEAS_THREADS = 256;
+constexpr int FINAL_THREADS = 1024;
+
+inline int meas_plaq_blocks(const GeomH& g) { return int((2LL * g.Vh + MEAS_THREADS - 1) / MEAS_THREADS); }
+inline int meas_poly_blocks(const GeomH& g) {
+  return int(((long long)g.Ns * g.Ns * g.Ns + MEAS_THREADS - 1) / MEAS_THREADS);
+}
+inline size_t measure_partials(const GeomH& g) { return 2 * size_t(meas_plaq_blocks(g) + meas_poly_blocks(g)); }
+
+enum { KIND_HB = 0, KIND_OR = 1 };
+
+// One table per (group, storage).
+struct PolicyOps {
+  int group;
+  int precision;   // 0 = FP64 plain, 1 = FP32 compressed
+  int comps;       // 16-byte vectors per link
+  cudaError_t (*phase)(const Ctx&, int kind, int parity, int mu, int block, cudaStream_t);
+  cudaError_t (*reunit)(const Ctx&, int advance_sweep, cudaStream_t);
+  cudaError_t (*start)(const Ctx&, int hot, cudaStream_t);
+  cudaError_t (*measure)(const Ctx&, int effective, cudaStream_t);
+  cudaError_t (*to_canonical)(const Ctx&, double* dev_out, cudaStream_t);
+  cudaError_t (*from_canonical)(const Ctx&, const double* dev_in, cudaStream_t);
+};
+
+extern const PolicyOps kOpsSU2F64;
+extern const PolicyOps kOpsSU2F32;
+extern const PolicyOps kOpsSU3F64;
+extern const PolicyOps kOpsSU3F32;
+
+}  // namespace qcd

@@ -1,0 +1,740 @@
+// qcd_kernels.cuh -- templated kernels of the gauge sweep.  Each storage
+// translation unit (su2_f32.cu, su2_f64.cu, su3_f32.cu, su3_f64.cu)
+// instantiates them for one (group, precision) and exports a PolicyOps table.
+//
+// Link layout in device memory (the paper's sec. 3.3 scheme of 4-vectors with
+// the site index fastest, split by checkerboard parity): 16-byte vectors,
+// vector (comp, mu, parity, h) at ((comp * 4 + mu) * 2 + parity) * plane + h,
+// h = s >> 1 the index inside the parity.  Per link:
+//   SU(2) FP32  1 x float4   (q0, q1, q2, q3)
+//   SU(2) FP64  2 x double2  (q0, q1) (q2, q3)
+//   SU(3) FP32  3 x float4   rows 0-1: (u00, u01) (u02, u10) (u11, u12)
+//   SU(3) FP64  9 x double2  u_rc, r-major
+#pragma once
+
+#include "qcd_device.cuh"
+#include "qcd_internal.h"
+
+namespace qcd {
+
+// ---------------------------------------------------------------------------
+// Storage policies
+// ---------------------------------------------------------------------------
+template <typename R>
+struct SU2Policy;
+
+template <>
+struct SU2Policy<float> {
+  using Real = float;
+  using Link = Quat<float>;
+  static constexpr int N = 2, COMPS = 1;
+  static __device__ __forceinline__ Link load(const void* base, const Geom& g, int mu, int par, int h) {
+    const float4 v = __ldg(reinterpret_cast<const float4*>(base) + vidx(g, 0, mu, par, h));
+    return {v.x, v.y, v.z, v.w};
+  }
+  static __device__ __forceinline__ void store(void* base, const Geom& g, int mu, int par, int h, const Link& u) {
+    reinterpret_cast<float4*>(base)[vidx(g, 0, mu, par, h)] = make_float4(u.q0, u.q1, u.q2, u.q3);
+  }
+};
+
+template <>
+struct SU2Policy<double> {
+  using Real = double;
+  using Link = Quat<double>;
+  static constexpr int N = 2, COMPS = 2;
+  static __device__ __forceinline__ Link load(const void* base, const Geom& g, int mu, int par, int h) {
+    const double2* p = reinterpret_cast<const double2*>(base);
+    const double2 a = __ldg(p + vidx(g, 0, mu, par, h)), b = __ldg(p + vidx(g, 1, mu, par, h));
+    return {a.x, a.y, b.x, b.y};
+  }
+  static __device__ __forceinline__ void store(void* base, const Geom& g, int mu, int par, int h, const Link& u) {
+    double2* p = reinterpret_cast<double2*>(base);
+    p[vidx(g, 0, mu, par, h)] = make_double2(u.q0, u.q1);
+    p[vidx(g, 1, mu, par, h)] = make_double2(u.q2, u.q3);
+  }
+};
+
+template <typename R>
+struct SU3Policy;
+
+template <>
+struct SU3Policy<float> {
+  using Real = float;
+  using Link = M3<float>;
+  static constexpr int N = 3, COMPS = 3;
+  static __device__ __forceinline__ Link load(const void* base, const Geom& g, int mu, int par, int h) {
+    const float4* p = reinterpret_cast<const float4*>(base);
+    const float4 a = __ldg(p + vidx(g, 0, mu, par, h));
+    const float4 b = __ldg(p + vidx(g, 1, mu, par, h));
+    const float4 c = __ldg(p + vidx(g, 2, mu, par, h));
+    Link m;
+    m.e[0][0] = {a.x, a.y};
+    m.e[0][1] = {a.z, a.w};
+    m.e[0][2] = {b.x, b.y};
+    m.e[1][0] = {b.z, b.w};
+    m.e[1][1] = {c.x, c.y};
+    m.e[1][2] = {c.z, c.w};
+    m3_rebuild_row2(m);
+    return m;
+  }
+  static __device__ __forceinline__ void store(void* base, const Geom& g, int mu, int par, int h, const Link& m) {
+    float4* p = reinterpret_cast<float4*>(base);
+    p[vidx(g, 0, mu, par, h)] = make_float4(m.e[0][0].re, m.e[0][0].im, m.e[0][1].re, m.e[0][1].im);
+    p[vidx(g, 1, mu, par, h)] = make_float4(m.e[0][2].re, m.e[0][2].im, m.e[1][0].re, m.e[1][0].im);
+    p[vidx(g, 2, mu, par, h)] = make_float4(m.e[1][1].re, m.e[1][1].im, m.e[1][2].re, m.e[1][2].im);
+  }
+};
+
+template <>
+struct SU3Policy<double> {
+  using Real = double;
+  using Link = M3<double>;
+  static constexpr int N = 3, COMPS = 9;
+  static __device__ __forceinline__ Link load(const void* base, const Geom& g, int mu, int par, int h) {
+    const double2* p = reinterpret_cast<const double2*>(base);
+    Link m;
+#pragma unroll
+    for (int k = 0; k < 9; ++k) {
+      const double2 v = __ldg(p + vidx(g, k, mu, par, h));
+      m.e[k / 3][k % 3] = {v.x, v.y};
+    }
+    return m;
+  }
+  static __device__ __forceinline__ void store(void* base, const Geom& g, int mu, int par, int h, const Link& m) {
+    double2* p = reinterpret_cast<double2*>(base);
+#pragma unroll
+    for (int k = 0; k < 9; ++k) p[vidx(g, k, mu, par, h)] = make_double2(m.e[k / 3][k % 3].re, m.e[k / 3][k % 3].im);
+  }
+};
+
+// ---------------------------------------------------------------------------
+// Group algebra used by the generic staple / plaquette code
+// ---------------------------------------------------------------------------
+template <typename R>
+struct Alg {
+  // SU(2) (quaternions)
+  static __device__ __forceinline__ void zero(Quat<R>& a) { a = {R(0), R(0), R(0), R(0)}; }
+  static __device__ __forceinline__ Quat<R> mul(const Quat<R>& a, const Quat<R>& b) { return qmul(a, b); }
+  static __device__ __forceinline__ Quat<R> mul_nd(const Quat<R>& a, const Quat<R>& b) { return qmul(a, qdag(b)); }
+  static __device__ __forceinline__ void acc_nd(Quat<R>& acc, const Quat<R>& a, const Quat<R>& b) {
+    acc = qadd(acc, qmul(a, qdag(b)));
+  }
+  static __device__ __forceinline__ void acc_dn(Quat<R>& acc, const Quat<R>& a, const Quat<R>& b) {
+    acc = qadd(acc, qmul(qdag(a), b));
+  }
+  // u B with B = diag(e^{i phi}, e^{-i phi}) = cos phi + i sin phi sigma3
+  static __device__ __forceinline__ Quat<R> right_phase(const Quat<R>& u, R c, R s) {
+    return qmul(u, Quat<R>{c, R(0), R(0), s});
+  }
+  // Re Tr(a b^+) / N
+  static __device__ __forceinline__ R retr_nd_over_n(const Quat<R>& a, const Quat<R>& b) {
+    return a.q0 * b.q0 + a.q1 * b.q1 + a.q2 * b.q2 + a.q3 * b.q3;
+  }
+
+  // SU(3) (3x3 matrices)
+  static __device__ __forceinline__ void zero(M3<R>& a) { m3_zero(a); }
+  static __device__ __forceinline__ M3<R> mul(const M3<R>& a, const M3<R>& b) { return m3_mul(a, b); }
+  static __device__ __forceinline__ M3<R> mul_nd(const M3<R>& a, const M3<R>& b) { return m3_mul_nd(a, b); }
+  static __device__ __forceinline__ void acc_nd(M3<R>& acc, const M3<R>& a, const M3<R>& b) { m3_acc_nd(acc, a, b); }
+  static __device__ __forceinline__ void acc_dn(M3<R>& acc, const M3<R>& a, const M3<R>& b) { m3_acc_dn(acc, a, b); }
+  // u B with B = diag(e^{i phi}, e^{-i phi}, 1)
+  static __device__ __forceinline__ M3<R> right_phase(M3<R> u, R c, R s) {
+    const Cx<R> p{c, s}, pc{c, -s};
+#pragma unroll
+    for (int r = 0; r < 3; ++r) {
+      u.e[r][0] = u.e[r][0] * p;
+      u.e[r][1] = u.e[r][1] * pc;
+    }
+    return u;
+  }
+  static __device__ __forceinline__ R retr_nd_over_n(const M3<R>& a, const M3<R>& b) {
+    R s = R(0);
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+      for (int j = 0; j < 3; ++j) s = fma(a.e[i][j].re, b.e[i][j].re, fma(a.e[i][j].im, b.e[i][j].im, s));
+    return s * R(1.0 / 3.0);
+  }
+};
+
+template <typename R>
+__device__ __forceinline__ void load_phase(const Ctx& a, int x, R& c, R& s);
+template <>
+__device__ __forceinline__ void load_phase<float>(const Ctx& a, int x, float& c, float& s) {
+  const float2 v = __ldg(a.phase32 + x);
+  c = v.x;
+  s = v.y;
+}
+template <>
+__device__ __forceinline__ void load_phase<double>(const Ctx& a, int x, double& c, double& s) {
+  const double2 v = __ldg(a.phase64 + x);
+  c = v.x;
+  s = v.y;
+}
+
+// Effective link Ut_mu(site) = U_mu(site) B_mu(site).
+template <class P, bool FIELD>
+__device__ __forceinline__ typename P::Link load_eff(const Ctx& a, int mu, const Site& c) {
+  using R = typename P::Real;
+  typename P::Link u = P::load(a.links, a.g, mu, parity_of(c), lex(a.g, c) >> 1);
+  if (FIELD && mu == 1) {
+    R ph_c, ph_s;
+    load_phase<R>(a, c.x, ph_c, ph_s);
+    u = Alg<R>::right_phase(u, ph_c, ph_s);
+  }
+  return u;
+}
+
+// Staple sum of U_mu(x) on effective links:
+//   A = sum_{nu != mu} Ut_nu(x+mu) Ut_mu(x+nu)^+ Ut_nu(x)^+
+//                    + (Ut_mu(x-nu) Ut_nu(x+mu-nu))^+ Ut_nu(x-nu)
+template <class P, bool FIELD>
+__device__ __forceinline__ typename P::Link staple(const Ctx& a, const Site& x, int mu) {
+  using R = typename P::Real;
+  using A = Alg<R>;
+  typename P::Link acc;
+  A::zero(acc);
+  const Site xp = step(a.g, x, mu, +1);
+#pragma unroll
+  for (int nu = 0; nu < 4; ++nu) {
+    if (nu == mu) continue;
+    const Site xpn = step(a.g, x, nu, +1);
+    const Site xmn = step(a.g, x, nu, -1);
+    const Site xpmn = step(a.g, xp, nu, -1);
+    {
+      const auto u1 = load_eff<P, FIELD>(a, nu, xp);
+      const auto u2 = load_eff<P, FIELD>(a, mu, xpn);
+      const auto u3 = load_eff<P, FIELD>(a, nu, x);
+      A::acc_nd(acc, A::mul_nd(u1, u2), u3);
+    }
+    {
+      const auto l1 = load_eff<P, FIELD>(a, nu, xpmn);
+      const auto l2 = load_eff<P, FIELD>(a, mu, xmn);
+      const auto l3 = load_eff<P, FIELD>(a, nu, xmn);
+      A::acc_dn(acc, A::mul(l2, l1), l3);
+    }
+  }
+  return acc;
+}
+
+// ---------------------------------------------------------------------------
+// SU(2) phase update: Kennedy-Pendleton heat-bath or overrelaxation of the
+// links of direction mu on sites of one parity.
+// ---------------------------------------------------------------------------
+template <typename R, bool FIELD, int KIND>
+__global__ void su2_phase_kernel(const Ctx a, int parity, int mu) {
+  using P = SU2Policy<R>;
+  const int h = blockIdx.x * blockDim.x + threadIdx.x;
+  if (h >= a.g.Vh) return;
+  const Site x = site_of(a.g, parity, h);
+  const Quat<R> A = staple<P, FIELD>(a, x, mu);
+  const R k = q_sqrt(qnorm2(A));  // sqrt(det A)
+  const bool phased = FIELD && mu == 1;
+  R bc = R(1), bs = R(0);
+  if (phased) load_phase<R>(a, x.x, bc, bs);
+  const Quat<R> Bd{bc, R(0), R(0), -bs};  // B^+
+
+  Quat<R> ut_new;
+  if (KIND == KIND_HB) {
+    const R alpha = R(a.beta) * k;
+    const uint32_t s = uint32_t(lex(a.g, x));
+    const uint32_t sweep = *a.sweep;
+    const Stream dir = make_stream(a.k0, a.k1, s, sweep, mu, 0, KIND_DIR);
+    if (alpha == R(0)) {
+      ut_new = su2_haar<R>(dir, 0u);
+    } else {
+      const Stream tries = make_stream(a.k0, a.k1, s, sweep, mu, 0, KIND_TRY);
+      R delta;
+      if (!kp_draw<R>(alpha, a.nhit, tries, delta)) {
+        atomicAdd(a.exhausted, 1ull);
+        return;  // keep the link
+      }
+      const Quat<R> X = su2_with_delta<R>(delta, dir);
+      const Quat<R> V = qscale(A, R(1) / k);
+      ut_new = qmul(X, qdag(V));
+    }
+  } else {
+    if (k == R(0)) return;
+    const Quat<R> Vd = qdag(qscale(A, R(1) / k));
+    Quat<R> ut = P::load(a.links, a.g, mu, parity, h);
+    if (phased) ut = qmul(ut, qdag(Bd));
+    ut_new = qmul(qmul(Vd, qdag(ut)), Vd);
+  }
+  const Quat<R> u_new = phased ? qmul(ut_new, Bd) : ut_new;
+  P::store(a.links, a.g, mu, parity, h, u_new);
+}
+
+// ---------------------------------------------------------------------------
+// SU(3) phase update: Cabibbo-Marinari heat-bath or overrelaxation over the
+// SU(2) subgroups (0,1), (1,2), (0,2).
+// ---------------------------------------------------------------------------
+template <typename R>
+__device__ __forceinline__ Quat<R> block_quat(const M3<R>& w, int i, int j) {
+  return {R(0.5) * (w.e[i][i].re + w.e[j][j].re), R(0.5) * (w.e[i][j].im + w.e[j][i].im),
+          R(0.5) * (w.e[i][j].re - w.e[j][i].re), R(0.5) * (w.e[i][i].im - w.e[j][j].im)};
+}
+
+// m <- R_emb m for the 2x2 matrix of quaternion r on rows (i, j).
+template <typename R>
+__device__ __forceinline__ void left_rotate(M3<R>& m, const Quat<R>& r, int i, int j) {
+  const Cx<R> r00{r.q0, r.q3}, r01{r.q2, r.q1}, r10{-r.q2, r.q1}, r11{r.q0, -r.q3};
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    const Cx<R> mi = m.e[i][c], mj = m.e[j][c];
+    m.e[i][c] = cfma(r01, mj, r00 * mi);
+    m.e[j][c] = cfma(r11, mj, r10 * mi);
+  }
+}
+
+template <typename R, bool FIELD, int KIND>
+__global__ void su3_phase_kernel(const Ctx a, int parity, int mu) {
+  using P = SU3Policy<R>;
+  const int h = blockIdx.x * blockDim.x + threadIdx.x;
+  if (h >= a.g.Vh) return;
+  const Site x = site_of(a.g, parity, h);
+  const M3<R> A = staple<P, FIELD>(a, x, mu);
+  M3<R> U = P::load(a.links, a.g, mu, parity, h);
+  M3<R> Ut = U;
+  if (FIELD && mu == 1) {
+    R bc, bs;
+    load_phase<R>(a, x.x, bc, bs);
+    Ut = Alg<R>::right_phase(U, bc, bs);
+  }
+  M3<R> W = m3_mul(Ut, A);
+  const uint32_t s = uint32_t(lex(a.g, x));
+  uint32_t sweep = 0;
+  if (KIND == KIND_HB) sweep = *a.sweep;
+  unsigned exhausted = 0;
+#pragma unroll
+  for (int sub = 0; sub < 3; ++sub) {
+    const int i = sub == 1 ? 1 : 0;
+    const int j = sub == 0 ? 1 : 2;
+    const Quat<R> w = block_quat(W, i, j);
+    const R k = q_sqrt(qnorm2(w));
+    Quat<R> r;
+    if (KIND == KIND_HB) {
+      const R alpha = R(2.0 / 3.0) * R(a.beta) * k;
+      const Stream dir = make_stream(a.k0, a.k1, s, sweep, mu, sub, KIND_DIR);
+      if (alpha == R(0)) {
+        r = su2_haar<R>(dir, 0u);
+      } else {
+        const Stream tries = make_stream(a.k0, a.k1, s, sweep, mu, sub, KIND_TRY);
+        R delta;
+        if (!kp_draw<R>(alpha, a.nhit, tries, delta)) {
+          ++exhausted;
+          continue;
+        }
+        const Quat<R> X = su2_with_delta<R>(delta, dir);
+        r = qmul(X, qdag(qscale(w, R(1) / k)));
+      }
+    } else {
+      if (k == R(0)) continue;
+      const Quat<R> vd = qdag(qscale(w, R(1) / k));
+      r = qmul(vd, vd);
+    }
+    left_rotate(U, r, i, j);
+    left_rotate(W, r, i, j);
+  }
+  if (exhausted) atomicAdd(a.exhausted, (unsigned long long)exhausted);
+  P::store(a.links, a.g, mu, parity, h, U);
+}
+
+// ---------------------------------------------------------------------------
+// FP64 reunitarization of every link (one thread per link); optionally
+// advances the sweep counter (the end of a sweep).
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void advance_if(const Ctx& a, int advance) {
+  if (advance && blockIdx.x == 0 && threadIdx.x == 0) *a.sweep_rw += 1u;
+}
+
+template <typename R>
+__global__ void su2_reunit_kernel(const Ctx a, int advance) {
+  using P = SU2Policy<R>;
+  advance_if(a, advance);
+  const int64_t idx = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (idx >= 8LL * a.g.Vh) return;
+  const int plane = int(idx / a.g.Vh), h = int(idx % a.g.Vh);
+  const int mu = plane >> 1, par = plane & 1;
+  const Quat<R> u = P::load(a.links, a.g, mu, par, h);
+  const double q0 = u.q0, q1 = u.q1, q2 = u.q2, q3 = u.q3;
+  const double inv = rsqrt(q0 * q0 + q1 * q1 + q2 * q2 + q3 * q3);
+  P::store(a.links, a.g, mu, par, h, Quat<R>{R(q0 * inv), R(q1 * inv), R(q2 * inv), R(q3 * inv)});
+}
+
+template <typename R>
+__global__ void su3_reunit_kernel(const Ctx a, int advance) {
+  using P = SU3Policy<R>;
+  advance_if(a, advance);
+  const int64_t idx = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (idx >= 8LL * a.g.Vh) return;
+  const int plane = int(idx / a.g.Vh), h = int(idx % a.g.Vh);
+  const int mu = plane >> 1, par = plane & 1;
+  const M3<R> u = P::load(a.links, a.g, mu, par, h);
+  M3<double> d;
+#pragma unroll
+  for (int r = 0; r < 2; ++r)
+#pragma unroll
+    for (int c = 0; c < 3; ++c) d.e[r][c] = {double(u.e[r][c].re), double(u.e[r][c].im)};
+  double n1 = 0.0;
+#pragma unroll
+  for (int c = 0; c < 3; ++c) n1 = fma(d.e[0][c].re, d.e[0][c].re, fma(d.e[0][c].im, d.e[0][c].im, n1));
+  const double i1 = rsqrt(n1);
+#pragma unroll
+  for (int c = 0; c < 3; ++c) d.e[0][c] = scale(d.e[0][c], i1);
+  Cx<double> proj{0.0, 0.0};
+#pragma unroll
+  for (int c = 0; c < 3; ++c) proj = cfma_cn(d.e[0][c], d.e[1][c], proj);
+#pragma unroll
+  for (int c = 0; c < 3; ++c) d.e[1][c] = d.e[1][c] - proj * d.e[0][c];
+  double n2 = 0.0;
+#pragma unroll
+  for (int c = 0; c < 3; ++c) n2 = fma(d.e[1][c].re, d.e[1][c].re, fma(d.e[1][c].im, d.e[1][c].im, n2));
+  const double i2 = rsqrt(n2);
+#pragma unroll
+  for (int c = 0; c < 3; ++c) d.e[1][c] = scale(d.e[1][c], i2);
+  m3_rebuild_row2(d);
+  M3<R> out;
+#pragma unroll
+  for (int r = 0; r < 3; ++r)
+#pragma unroll
+    for (int c = 0; c < 3; ++c) out.e[r][c] = {R(d.e[r][c].re), R(d.e[r][c].im)};
+  P::store(a.links, a.g, mu, par, h, out);
+}
+
+// ---------------------------------------------------------------------------
+// Start: cold (unit links) or hot (Haar links; SU(2) Shoemake, SU(3)
+// Mezzadri), generated in FP64 and rounded to the storage.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ M3<double> su3_haar_fp64(const Stream& st) {
+  double u[20];
+#pragma unroll
+  for (int b = 0; b < 5; ++b) st.uniforms<double>(uint32_t(b), u + 4 * b);
+  M3<double> z;
+#pragma unroll
+  for (int k = 0; k < 9; ++k) {
+    const double rad = sqrt(-2.0 * log(u[2 * k]));
+    double sn, cs;
+    sincospi(2.0 * u[2 * k + 1], &sn, &cs);
+    z.e[k / 3][k % 3] = {rad * cs, rad * sn};
+  }
+#pragma unroll
+  for (int r = 0; r < 3; ++r) {
+#pragma unroll
+    for (int q = 0; q < r; ++q) {
+      Cx<double> proj{0.0, 0.0};
+#pragma unroll
+      for (int c = 0; c < 3; ++c) proj = cfma_cn(z.e[q][c], z.e[r][c], proj);
+#pragma unroll
+      for (int c = 0; c < 3; ++c) z.e[r][c] = z.e[r][c] - proj * z.e[q][c];
+    }
+    double n = 0.0;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) n += z.e[r][c].re * z.e[r][c].re + z.e[r][c].im * z.e[r][c].im;
+    n = sqrt(n);
+#pragma unroll
+    for (int c = 0; c < 3; ++c) z.e[r][c] = {z.e[r][c].re / n, z.e[r][c].im / n};
+  }
+  // det, then multiply by det^(-1/3) on the principal branch
+  const Cx<double> d = z.e[0][0] * (z.e[1][1] * z.e[2][2] - z.e[1][2] * z.e[2][1]) -
+                       z.e[0][1] * (z.e[1][0] * z.e[2][2] - z.e[1][2] * z.e[2][0]) +
+                       z.e[0][2] * (z.e[1][0] * z.e[2][1] - z.e[1][1] * z.e[2][0]);
+  const double th = atan2(d.im, d.re);
+  double fs, fc;
+  sincos(-th / 3.0, &fs, &fc);
+  const Cx<double> fix{fc, fs};
+#pragma unroll
+  for (int r = 0; r < 3; ++r)
+#pragma unroll
+    for (int c = 0; c < 3; ++c) z.e[r][c] = z.e[r][c] * fix;
+  return z;
+}
+
+template <class P>
+__global__ void start_kernel(const Ctx a, int hot) {
+  using R = typename P::Real;
+  const int64_t idx = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (idx >= 8LL * a.g.Vh) return;
+  const int plane = int(idx / a.g.Vh), h = int(idx % a.g.Vh);
+  const int mu = plane >> 1, par = plane & 1;
+  const Site x = site_of(a.g, par, h);
+  const Stream st = make_stream(a.k0, a.k1, uint32_t(lex(a.g, x)), START_SWEEP_WORD, mu, 0, KIND_START);
+  typename P::Link u;
+  if constexpr (P::N == 2) {
+    const Quat<double> q = hot ? su2_haar<double>(st, 0u) : Quat<double>{1.0, 0.0, 0.0, 0.0};
+    u = {R(q.q0), R(q.q1), R(q.q2), R(q.q3)};
+  } else {
+    M3<double> m;
+    if (hot) {
+      m = su3_haar_fp64(st);
+    } else {
+      m3_zero(m);
+      m.e[0][0].re = m.e[1][1].re = m.e[2][2].re = 1.0;
+    }
+#pragma unroll
+    for (int r = 0; r < 3; ++r)
+#pragma unroll
+      for (int c = 0; c < 3; ++c) u.e[r][c] = {R(m.e[r][c].re), R(m.e[r][c].im)};
+  }
+  P::store(a.links, a.g, mu, par, h, u);
+}
+
+// ---------------------------------------------------------------------------
+// Measurements: plaquette (spatial / temporal split) and Polyakov loop.
+// Products in the storage precision, sums in FP64: per-thread value, warp
+// shuffle, per-block partial, then one block sums the partials in a fixed
+// order (deterministic for a given lattice).
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void block_sum2(double& v0, double& v1, double* partial_out) {
+  __shared__ double sh[2][MEAS_THREADS / 32];
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) {
+    v0 += __shfl_down_sync(0xffffffffu, v0, off);
+    v1 += __shfl_down_sync(0xffffffffu, v1, off);
+  }
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  if (lane == 0) {
+    sh[0][warp] = v0;
+    sh[1][warp] = v1;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double s0 = 0.0, s1 = 0.0;
+    for (int w = 0; w < MEAS_THREADS / 32; ++w) {
+      s0 += sh[0][w];
+      s1 += sh[1][w];
+    }
+    partial_out[0] = s0;
+    partial_out[1] = s1;
+  }
+}
+
+template <class P, bool FIELD>
+__global__ void __launch_bounds__(MEAS_THREADS) measure_kernel(const Ctx a, int n_plaq_blocks) {
+  using R = typename P::Real;
+  using A = Alg<R>;
+  double v0 = 0.0, v1 = 0.0;
+  if (int(blockIdx.x) < n_plaq_blocks) {
+    const int64_t idx = int64_t(blockIdx.x) * MEAS_THREADS + threadIdx.x;
+    if (idx < 2LL * a.g.Vh) {
+      const int par = int(idx / a.g.Vh), h = int(idx % a.g.Vh);
+      const Site x = site_of(a.g, par, h);
+#pragma unroll
+      for (int mu = 0; mu < 4; ++mu) {
+        const Site xpm = step(a.g, x, mu, +1);
+        const auto umu = load_eff<P, FIELD>(a, mu, x);
+#pragma unroll
+        for (int nu = mu + 1; nu < 4; ++nu) {
+          const Site xpn = step(a.g, x, nu, +1);
+          const auto ab = A::mul(umu, load_eff<P, FIELD>(a, nu, xpm));
+          const auto dc = A::mul(load_eff<P, FIELD>(a, nu, x), load_eff<P, FIELD>(a, mu, xpn));
+          const double p = double(A::retr_nd_over_n(ab, dc));
+          if (nu == 3) v1 += p;
+          else v0 += p;
+        }
+      }
+    }
+  } else {
+    const int64_t idx = int64_t(int(blockIdx.x) - n_plaq_blocks) * MEAS_THREADS + threadIdx.x;
+    const int64_t V3 = int64_t(a.g.Ns) * a.g.Ns * a.g.Ns;
+    if (idx < V3) {
+      Site x;
+      x.x = int(idx % a.g.Ns);
+      x.y = int((idx / a.g.Ns) % a.g.Ns);
+      x.z = int(idx / (int64_t(a.g.Ns) * a.g.Ns));
+      x.t = 0;
+      auto l = P::load(a.links, a.g, 3, parity_of(x), lex(a.g, x) >> 1);
+      for (int t = 1; t < a.g.Nt; ++t) {
+        x.t = t;
+        l = A::mul(l, P::load(a.links, a.g, 3, parity_of(x), lex(a.g, x) >> 1));
+      }
+      if constexpr (P::N == 2) {
+        v0 = double(l.q0);
+      } else {
+        v0 = (double(l.e[0][0].re) + double(l.e[1][1].re) + double(l.e[2][2].re)) / 3.0;
+        v1 = (double(l.e[0][0].im) + double(l.e[1][1].im) + double(l.e[2][2].im)) / 3.0;
+      }
+    }
+  }
+  block_sum2(v0, v1, a.partials + 2 * blockIdx.x);
+}
+
+// Sums the per-block partials in a fixed order and normalises:
+// out = {P, P_s, P_t, Re L, Im L}.
+static __global__ void __launch_bounds__(FINAL_THREADS)
+    measure_final_kernel(const Ctx a, int n_plaq_blocks, int n_poly_blocks) {
+  __shared__ double sh[4][FINAL_THREADS];
+  double s[4] = {0.0, 0.0, 0.0, 0.0};
+  for (int b = threadIdx.x; b < n_plaq_blocks; b += FINAL_THREADS) {
+    s[0] += a.partials[2 * b];
+    s[1] += a.partials[2 * b + 1];
+  }
+  for (int b = threadIdx.x; b < n_poly_blocks; b += FINAL_THREADS) {
+    s[2] += a.partials[2 * (n_plaq_blocks + b)];
+    s[3] += a.partials[2 * (n_plaq_blocks + b) + 1];
+  }
+#pragma unroll
+  for (int k = 0; k < 4; ++k) sh[k][threadIdx.x] = s[k];
+  __syncthreads();
+  for (int w = FINAL_THREADS / 2; w > 0; w >>= 1) {
+    if (int(threadIdx.x) < w) {
+#pragma unroll
+      for (int k = 0; k < 4; ++k) sh[k][threadIdx.x] += sh[k][threadIdx.x + w];
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    const double V = 2.0 * double(a.g.Vh);
+    const double V3 = double(a.g.Ns) * a.g.Ns * a.g.Ns;
+    a.meas_out[0] = (sh[0][0] + sh[1][0]) / (6.0 * V);
+    a.meas_out[1] = sh[0][0] / (3.0 * V);
+    a.meas_out[2] = sh[1][0] / (3.0 * V);
+    a.meas_out[3] = sh[2][0] / V3;
+    a.meas_out[4] = sh[3][0] / V3;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Canonical FP64 layout [s][mu][row][col][re,im] <-> device storage
+// ---------------------------------------------------------------------------
+template <class P>
+__global__ void to_canonical_kernel(const Ctx a, double* out) {
+  const int64_t idx = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  const int64_t V = 2LL * a.g.Vh;
+  if (idx >= 4 * V) return;
+  const int s = int(idx >> 2), mu = int(idx & 3);
+  Site x;
+  x.x = s % a.g.Ns;
+  x.y = (s / a.g.Ns) % a.g.Ns;
+  x.z = (s / (a.g.Ns * a.g.Ns)) % a.g.Ns;
+  x.t = s / (a.g.Ns * a.g.Ns * a.g.Ns);
+  const auto u = P::load(a.links, a.g, mu, parity_of(x), s >> 1);
+  constexpr int N = P::N;
+  double* o = out + idx * (2 * N * N);
+  if constexpr (N == 2) {
+    const double q0 = u.q0, q1 = u.q1, q2 = u.q2, q3 = u.q3;
+    o[0] = q0; o[1] = q3;    // u00 = q0 + i q3
+    o[2] = q2; o[3] = q1;    // u01 = q2 + i q1
+    o[4] = -q2; o[5] = q1;   // u10 = -q2 + i q1
+    o[6] = q0; o[7] = -q3;   // u11 = q0 - i q3
+  } else {
+#pragma unroll
+    for (int r = 0; r < 3; ++r)
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        o[2 * (3 * r + c)] = u.e[r][c].re;
+        o[2 * (3 * r + c) + 1] = u.e[r][c].im;
+      }
+  }
+}
+
+template <class P>
+__global__ void from_canonical_kernel(const Ctx a, const double* in) {
+  using R = typename P::Real;
+  const int64_t idx = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  const int64_t V = 2LL * a.g.Vh;
+  if (idx >= 4 * V) return;
+  const int s = int(idx >> 2), mu = int(idx & 3);
+  Site x;
+  x.x = s % a.g.Ns;
+  x.y = (s / a.g.Ns) % a.g.Ns;
+  x.z = (s / (a.g.Ns * a.g.Ns)) % a.g.Ns;
+  x.t = s / (a.g.Ns * a.g.Ns * a.g.Ns);
+  constexpr int N = P::N;
+  const double* o = in + idx * (2 * N * N);
+  typename P::Link u;
+  if constexpr (N == 2) {
+    // SU(2) projection of the 2x2 matrix
+    u.q0 = R(0.5 * (o[0] + o[6]));
+    u.q1 = R(0.5 * (o[3] + o[5]));
+    u.q2 = R(0.5 * (o[2] - o[4]));
+    u.q3 = R(0.5 * (o[1] - o[7]));
+  } else {
+#pragma unroll
+    for (int r = 0; r < 3; ++r)
+#pragma unroll
+      for (int c = 0; c < 3; ++c) u.e[r][c] = {R(o[2 * (3 * r + c)]), R(o[2 * (3 * r + c) + 1])};
+  }
+  P::store(a.links, a.g, mu, parity_of(x), s >> 1, u);
+}
+
+// ---------------------------------------------------------------------------
+// Launchers
+// ---------------------------------------------------------------------------
+inline unsigned grid_for(int64_t n, int block) { return unsigned((n + block - 1) / block); }
+
+template <class P, bool FIELD, int KIND>
+inline void launch_phase_t(const Ctx& a, int parity, int mu, int block, cudaStream_t st) {
+  const unsigned grid = grid_for(a.g.Vh, block);
+  if constexpr (P::N == 2)
+    su2_phase_kernel<typename P::Real, FIELD, KIND><<<grid, block, 0, st>>>(a, parity, mu);
+  else
+    su3_phase_kernel<typename P::Real, FIELD, KIND><<<grid, block, 0, st>>>(a, parity, mu);
+}
+
+template <class P>
+cudaError_t launch_phase(const Ctx& a, int kind, int parity, int mu, int block, cudaStream_t st) {
+  const bool field = a.flux != 0;
+  if (kind == KIND_HB) {
+    if (field) launch_phase_t<P, true, KIND_HB>(a, parity, mu, block, st);
+    else launch_phase_t<P, false, KIND_HB>(a, parity, mu, block, st);
+  } else {
+    if (field) launch_phase_t<P, true, KIND_OR>(a, parity, mu, block, st);
+    else launch_phase_t<P, false, KIND_OR>(a, parity, mu, block, st);
+  }
+  return cudaGetLastError();
+}
+
+template <class P>
+cudaError_t launch_reunit(const Ctx& a, int advance, cudaStream_t st) {
+  const int block = 256;
+  if constexpr (P::N == 2)
+    su2_reunit_kernel<typename P::Real><<<grid_for(8LL * a.g.Vh, block), block, 0, st>>>(a, advance);
+  else
+    su3_reunit_kernel<typename P::Real><<<grid_for(8LL * a.g.Vh, block), block, 0, st>>>(a, advance);
+  return cudaGetLastError();
+}
+
+template <class P>
+cudaError_t launch_start(const Ctx& a, int hot, cudaStream_t st) {
+  const int block = 128;
+  start_kernel<P><<<grid_for(8LL * a.g.Vh, block), block, 0, st>>>(a, hot);
+  return cudaGetLastError();
+}
+
+template <class P>
+cudaError_t launch_measure(const Ctx& a, int effective, cudaStream_t st) {
+  const int np = meas_plaq_blocks(a.g), nl = meas_poly_blocks(a.g);
+  if (effective && a.flux != 0)
+    measure_kernel<P, true><<<np + nl, MEAS_THREADS, 0, st>>>(a, np);
+  else
+    measure_kernel<P, false><<<np + nl, MEAS_THREADS, 0, st>>>(a, np);
+  measure_final_kernel<<<1, FINAL_THREADS, 0, st>>>(a, np, nl);
+  return cudaGetLastError();
+}
+
+template <class P>
+cudaError_t launch_to_canonical(const Ctx& a, double* out, cudaStream_t st) {
+  to_canonical_kernel<P><<<grid_for(8LL * a.g.Vh, 256), 256, 0, st>>>(a, out);
+  return cudaGetLastError();
+}
+
+template <class P>
+cudaError_t launch_from_canonical(const Ctx& a, const double* in, cudaStream_t st) {
+  from_canonical_kernel<P><<<grid_for(8LL * a.g.Vh, 256), 256, 0, st>>>(a, in);
+  return cudaGetLastError();
+}
+
+template <class P>
+constexpr PolicyOps make_ops(int precision) {
+  return PolicyOps{P::N,
+                   precision,
+                   P::COMPS,
+                   &launch_phase<P>,
+                   &launch_reunit<P>,
+                   &launch_start<P>,
+                   &launch_measure<P>,
+                   &launch_to_canonical<P>,
+                   &launch_from_canonical<P>};
+}
+
+}  // namespace qcd

@@ -1,0 +1,6 @@
+// su2_f64.cu -- kernels of the gauge sweep instantiated for one (group, storage).
+#include "qcd_kernels.cuh"
+
+namespace qcd {
+const PolicyOps kOpsSU2F64 = make_ops<SU2Policy<double>>(0);
+}  // namespace qcd

@@ -1,0 +1,78 @@
+"""Parity at full size: SU(3) 64^3 x 16 (4.2M sites), beta 6.2, flux n = 1,
+FP32-compressed links, in the launch configuration the benchmark times
+(autotuned block size, graph-launched sweeps).  The oracle recomputes sampled
+links one by one from the same pre-phase state; untouched links must be
+bit-identical; the plaquette of one configuration must agree to 1e-6."""
+import numpy as np
+import pytest
+
+import oracle
+import workloads
+from workloads import FP32_COMPRESSED, HOT
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def q():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("needs a CUDA device")
+    from paper_1310_7087_gb300 import build
+    build.build()
+    import paper_1310_7087_gb300 as q
+    oracle.build()
+    return q
+
+
+def parity_sites(Ns, Nt, parity, n, rng):
+    V = Ns ** 3 * Nt
+    out = []
+    while len(out) < n:
+        s = int(rng.integers(0, V))
+        x, y, z, t = s % Ns, (s // Ns) % Ns, (s // Ns ** 2) % Ns, s // Ns ** 3
+        if (x + y + z + t) % 2 == parity:
+            out.append(s)
+    return out
+
+
+def test_full_size_sampled_phases(q):
+    w = workloads.SU3_64x16
+    lat = q.Lattice(3, w.Ns, w.Nt, w.beta, w.flux, FP32_COMPRESSED, HOT, w.seed)
+    lat.sweep(1, w.n_or, w.seed)
+    U0 = lat.get_links()
+    orc = oracle.OracleLattice(3, w.Ns, w.Nt, w.beta, w.flux, 10, 0)
+    orc.set_links(U0)
+    orc.sweep_counter = lat.sweep_counter
+
+    # one configuration: plaquette and Polyakov loop (FP32 products, FP64 sums)
+    (gp, gl), (op, ol) = lat.measure(), orc.measure()
+    assert np.abs(np.array(gp) - op).max() <= 1e-6, (gp, op)
+    assert np.abs(np.array(gl) - ol).max() <= 1e-6, (gl, ol)
+
+    rng = np.random.default_rng(0)
+    for kind, parity, mu in [(q.QCD_HEATBATH, 0, 1), (q.QCD_OVERRELAX, 1, 3), (q.QCD_HEATBATH, 1, 0)]:
+        lat.phase(kind, parity, mu, w.seed)
+        U1 = lat.get_links()
+        bad = 0
+        sites = parity_sites(w.Ns, w.Nt, parity, 1500, rng)
+        for s in sites:
+            ref, _ = orc.link_update(kind, s, mu, w.seed)
+            if np.abs(ref - U1[s, mu]).max() > 1e-5:
+                bad += 1
+        assert bad == 0, (kind, parity, mu, bad)  # >= 99.99% of 1500 samples
+        # nothing but the links of this phase changed
+        changed = np.any(U1 != U0, axis=(2, 3))
+        xs = np.arange(w.volume)
+        par = ((xs % w.Ns) + (xs // w.Ns) % w.Ns + (xs // w.Ns ** 2) % w.Ns + xs // w.Ns ** 3) % 2
+        allowed = np.zeros_like(changed)
+        allowed[par == parity, mu] = True
+        assert not np.any(changed & ~allowed)
+        U0 = U1
+        orc.set_links(U0)
+    # unitarity on a sample of the final configuration
+    sample = U0.reshape(-1, 3, 3)[rng.integers(0, 4 * w.volume, size=20000)]
+    err = np.abs(np.einsum("nki,nkj->nij", sample.conj(), sample) - np.eye(3)).max()
+    assert err < 2e-6, err
+    lat.close()
+    orc.close()

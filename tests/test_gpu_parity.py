@@ -1,0 +1,275 @@
+"""Parity of the CUDA sweep (through the C ABI) with the FP64 CPU oracle.
+
+Bars:
+  FP64 plain storage      every link within 1e-9 after one sweep (rounding
+                          order only, amplified by the chaotic chain),
+                          measurements within 1e-12;
+  FP32 compressed storage at least 99.99% of links within 1e-5 (max abs over
+                          the link's reals) after every kernel of the sweep
+                          schedule from a shared state, and after one short
+                          sweep (SU(2) HB + 1 OR, SU(3) HB, SU(3) 16^3 x 4
+                          HB + 1 OR); links that diverge on an accept/reject
+                          branch are counted; plaquette of one configuration
+                          |dP| <= 1e-6.
+The chain amplifies any perturbation: with FP32 rounding of the stored links as
+the only difference, the oracle itself ends one SU(3) HB + 4 OR sweep up to
+2e-2 away from its pure FP64 run.  The FP32 path is therefore held to the link
+bar kernel by kernel, and to the FP64 chain statistically (ensemble test).
+"""
+import numpy as np
+import pytest
+
+import oracle
+from workloads import FP32_COMPRESSED, FP64_PLAIN, HOT, COLD
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def q():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("needs a CUDA device")
+    from paper_1310_7087_gb300 import build
+    build.build()
+    import paper_1310_7087_gb300 as q
+    oracle.build()
+    return q
+
+
+def link_err(a, b):
+    V = a.shape[0]
+    return np.abs(a - b).reshape(V * 4, -1).max(axis=1)
+
+
+def check_links(a, b, precision, what=""):
+    err = link_err(a, b)
+    if precision == FP64_PLAIN:
+        assert err.max() < 1e-9, (what, err.max())
+    else:
+        frac = (err <= 1e-5).mean()
+        assert frac >= 0.9999, (what, frac, int((err > 1e-5).sum()), err.max())
+    return err
+
+
+# (group, precision, Ns, Nt, beta, flux): several tiles, ragged tails (Vh = 432,
+# 216), the degenerate 2^4 lattice, field on and off.
+CASES = [
+    (2, FP64_PLAIN, 4, 4, 2.3, 0),
+    (2, FP32_COMPRESSED, 4, 4, 2.3, 0),
+    (2, FP64_PLAIN, 6, 4, 2.3, 2),
+    (2, FP32_COMPRESSED, 6, 4, 2.3, 2),
+    (2, FP64_PLAIN, 2, 2, 2.0, 1),
+    (3, FP64_PLAIN, 4, 4, 5.7, 0),
+    (3, FP32_COMPRESSED, 4, 4, 5.7, 0),
+    (3, FP64_PLAIN, 6, 2, 6.0, 1),
+    (3, FP32_COMPRESSED, 6, 2, 6.0, 1),
+    (3, FP32_COMPRESSED, 8, 6, 6.0, 4),
+    (3, FP64_PLAIN, 2, 2, 5.0, 1),
+]
+IDS = ["su%d_%s_%dx%d_b%g_n%d" % (g, "f64" if p == FP64_PLAIN else "f32", ns, nt, b, f)
+       for g, p, ns, nt, b, f in CASES]
+
+
+def pair(q, case, start=HOT, seed=7, nhit=10):
+    g, p, ns, nt, beta, flux = case
+    lat = q.Lattice(g, ns, nt, beta, flux, p, start, seed, nhit=nhit)
+    orc = oracle.OracleLattice(g, ns, nt, beta, flux, nhit, 0)
+    return lat, orc
+
+
+@pytest.mark.parametrize("case", CASES, ids=IDS)
+def test_hot_start_matches_oracle(q, case):
+    lat, orc = pair(q, case)
+    orc.hot_start(7)
+    tol = 1e-13 if case[1] == FP64_PLAIN else 2e-7
+    assert link_err(lat.get_links(), orc.get_links()).max() < tol
+    lat.close()
+
+
+WHOLE_SWEEP = [c for c in CASES if c[1] == FP64_PLAIN or c[0] == 2]
+
+
+@pytest.mark.parametrize("case", WHOLE_SWEEP, ids=[IDS[CASES.index(c)] for c in WHOLE_SWEEP])
+def test_one_sweep_from_shared_start(q, case):
+    """FP64 storage (both groups) and FP32 SU(2): one whole graph-launched
+    sweep, HB + 4 OR (SU(3)) or HB + 1 OR (SU(2)), from a shared start."""
+    lat, orc = pair(q, case)
+    orc.set_links(lat.get_links())
+    n_or = 4 if case[0] == 3 else 1
+    lat.sweep(1, n_or, 7)
+    orc.sweep(1, n_or, 7)
+    check_links(lat.get_links(), orc.get_links(), case[1], "sweep")
+    assert lat.sweep_counter == 1 == orc.sweep_counter
+    lat.close()
+
+
+def run_kernel_by_kernel(q, case, seed=7):
+    """Every kernel of one HB + n_or OR sweep (n_or = 4 for SU(3)) and the
+    reunitarization, each from the state the previous GPU kernel left, against
+    the oracle started from that same state."""
+    lat, orc = pair(q, case, seed=seed)
+    lat.sweep(1, 1, seed)  # launch shape chosen as in a normal run
+    n_or = 4 if case[0] == 3 else 1
+    schedule = [(q.QCD_HEATBATH, p, mu) for p in (0, 1) for mu in range(4)]
+    schedule += [(q.QCD_OVERRELAX, p, mu) for _ in range(n_or) for p in (0, 1) for mu in range(4)]
+    schedule += [("reunitarize", 0, 0)]
+    for kind, parity, mu in schedule:
+        orc.set_links(lat.get_links())
+        orc.sweep_counter = lat.sweep_counter
+        if kind == "reunitarize":
+            lat.reunitarize()
+            orc.reunitarize()
+        else:
+            lat.phase(kind, parity, mu, seed)
+            orc.phase(kind, parity, mu, seed)
+        check_links(lat.get_links(), orc.get_links(), case[1], (kind, parity, mu))
+    lat.close()
+
+
+@pytest.mark.parametrize("case", CASES, ids=IDS)
+def test_sweep_schedule_kernel_by_kernel(q, case):
+    run_kernel_by_kernel(q, case)
+
+
+def test_su3_16x4_fp32_kernel_by_kernel(q):
+    """SU(3) 16^3 x 4, beta 5.7, hot start seed 7, FP32-compressed links: the
+    whole HB + 4 OR + reunitarization schedule, 65536 links per check."""
+    run_kernel_by_kernel(q, (3, FP32_COMPRESSED, 16, 4, 5.7, 0))
+
+
+@pytest.mark.parametrize("case", CASES, ids=IDS)
+def test_measurements_on_one_configuration(q, case):
+    lat, orc = pair(q, case)
+    lat.sweep(2, 1, 11)
+    orc.set_links(lat.get_links())
+    (gp, gl), (op, ol) = lat.measure(), orc.measure()
+    tol = 1e-12 if case[1] == FP64_PLAIN else 1e-6
+    assert np.abs(np.array(gp) - op).max() <= tol, (gp, op)
+    assert np.abs(np.array(gl) - ol).max() <= tol, (gl, ol)
+    assert np.abs(np.array(lat.measure_bare()) - orc.measure_bare()).max() <= tol
+    lat.close()
+
+
+@pytest.mark.parametrize("case", [CASES[2], CASES[3], CASES[7], CASES[8]], ids=[IDS[2], IDS[3], IDS[7], IDS[8]])
+def test_every_single_phase(q, case):
+    lat, orc = pair(q, case)
+    lat.sweep(1, 1, 3)
+    for kind in (q.QCD_HEATBATH, q.QCD_OVERRELAX):
+        for parity in (0, 1):
+            for mu in range(4):
+                orc.set_links(lat.get_links())
+                orc.sweep_counter = lat.sweep_counter
+                lat.phase(kind, parity, mu, 21)
+                orc.phase(kind, parity, mu, 21)
+                check_links(lat.get_links(), orc.get_links(), case[1], (kind, parity, mu))
+    lat.close()
+
+
+@pytest.mark.parametrize("group", [2, 3])
+@pytest.mark.parametrize("precision", [FP64_PLAIN, FP32_COMPRESSED])
+def test_cold_start_and_flux_closed_form(q, group, precision):
+    from test_oracle_lattice import flux_closed_form
+    for Ns, n in [(4, 1), (6, 2), (8, 3)]:
+        lat = q.Lattice(group, Ns, 2, 6.0, n, precision, COLD, 1)
+        plaq, poly = lat.measure()
+        tol = 1e-12 if precision == FP64_PLAIN else 1e-6
+        np.testing.assert_allclose(plaq, flux_closed_form(group, Ns, n), atol=tol)
+        np.testing.assert_allclose(poly, [1.0, 0.0], atol=tol)
+        np.testing.assert_allclose(lat.measure_bare(), [1.0, 1.0, 1.0], atol=tol)
+        lat.close()
+
+
+@pytest.mark.parametrize("group", [2, 3])
+def test_beta_zero_haar_branch(q, group):
+    case = (group, FP64_PLAIN, 4, 2, 0.0, 1)
+    lat, orc = pair(q, case, start=COLD)
+    lat.sweep(1, 0, 5)
+    orc.sweep(1, 0, 5)
+    check_links(lat.get_links(), orc.get_links(), FP64_PLAIN, "beta=0")
+    lat.close()
+
+
+@pytest.mark.parametrize("group", [2, 3])
+def test_nhit_exhaustion_count(q, group):
+    case = (group, FP64_PLAIN, 4, 4, 0.05, 0)
+    lat, orc = pair(q, case, nhit=1)
+    orc.set_links(lat.get_links())
+    lat.sweep(1, 0, 9)
+    orc.sweep(1, 0, 9)
+    assert orc.exhausted > 0
+    assert lat.exhausted == orc.exhausted
+    check_links(lat.get_links(), orc.get_links(), FP64_PLAIN, "nhit=1")
+    lat.close()
+
+
+@pytest.mark.parametrize("precision", [FP64_PLAIN, FP32_COMPRESSED])
+def test_set_get_round_trip(q, precision):
+    lat = q.Lattice(3, 4, 2, 5.0, 0, precision, HOT, 3)
+    orc = oracle.OracleLattice(3, 4, 2, 5.0, 0, 10, 0)
+    orc.hot_start(99)
+    ref = orc.get_links()
+    lat.set_links(ref)
+    tol = 0.0 if precision == FP64_PLAIN else 6e-7
+    assert link_err(lat.get_links(), ref).max() <= tol
+    lat.close()
+
+
+def test_bad_arguments_are_errors(q):
+    for args in [(4, 4, 4, 1.0), (2, 3, 4, 1.0), (2, 4, 5, 1.0), (3, 0, 4, 1.0), (3, 4, 4, -1.0)]:
+        with pytest.raises(q.QcdError) as e:
+            q.Lattice(*args)
+        assert e.value.code == q.QCD_ERR_INVALID_ARG
+    lat = q.Lattice(2, 4, 2, 1.0)
+    with pytest.raises(q.QcdError):
+        q.qcd_phase(lat.h, 5, 0, 0, 1)
+    with pytest.raises(q.QcdError):
+        q.qcd_set_nhit(lat.h, 0)
+    with pytest.raises(q.QcdError):
+        q.qcd_sweep(lat.h, -1, 0, 1)
+    lat.close()
+
+
+def binned(x, b=20):
+    x = np.asarray(x)
+    n = len(x) // b
+    m = x[: n * b].reshape(n, b).mean(1)
+    return m.mean(), m.std(ddof=1) / np.sqrt(n)
+
+
+@pytest.mark.parametrize("precision", [FP64_PLAIN, FP32_COMPRESSED])
+def test_ensemble_su3_6x4(q, precision):
+    """SU(3) 6^3 x 4, beta 5.7, hot start, 1 HB + 4 OR per sweep: 400 sweeps
+    on the GPU against an independent oracle chain, <P> within 3 sigma."""
+    lat = q.Lattice(3, 6, 4, 5.7, 0, precision, HOT, 3)
+    orc = oracle.OracleLattice(3, 6, 4, 5.7, 0, 10, 0)
+    orc.hot_start(4)
+    g_p, o_p = [], []
+    for i in range(440):
+        lat.sweep(1, 4, 3)
+        orc.sweep(1, 4, 4)
+        if i >= 40:
+            g_p.append(lat.measure()[0][0])
+            o_p.append(orc.measure()[0][0])
+    (ma, ea), (mb, eb) = binned(g_p), binned(o_p)
+    assert abs(ma - mb) < 3 * np.hypot(ea, eb), (ma, ea, mb, eb)
+    lat.close()
+
+
+@pytest.mark.parametrize("precision", [FP64_PLAIN, FP32_COMPRESSED])
+def test_ensemble_su2_4x4(q, precision):
+    """SU(2) 4^3 x 4, beta 2.3, cold start, 1 HB + 1 OR: 10^3 sweeps on the GPU
+    and an independent oracle chain agree within 3 sigma in <P> and <L>."""
+    lat = q.Lattice(2, 4, 4, 2.3, 0, precision, COLD, 1)
+    orc = oracle.OracleLattice(2, 4, 4, 2.3, 0, 10, 0)
+    g_p, g_l, o_p, o_l = [], [], [], []
+    for i in range(1100):
+        lat.sweep(1, 1, 1)
+        orc.sweep(1, 1, 2)
+        if i >= 100:
+            (p, l), (op, ol) = lat.measure(), orc.measure()
+            g_p.append(p[0]); g_l.append(l[0]); o_p.append(op[0]); o_l.append(ol[0])
+    for a, b in ((g_p, o_p), (g_l, o_l)):
+        (ma, ea), (mb, eb) = binned(a), binned(b)
+        assert abs(ma - mb) < 3 * np.hypot(ea, eb) + 1e-12, (ma, ea, mb, eb)
+    lat.close()
