@@ -310,12 +310,13 @@ int autotune(qcd_lattice* L) {
   QCD_CUDA(cudaEventCreate(&e0));
   QCD_CUDA(cudaEventCreate(&e1));
   const int cand[] = {64, 128, 256, 512};
+  const int limit = L->ops->max_phase_block();
   int best = 0;
   float best_ms = 1e30f;
   for (int c = 0; c < 4; ++c) {
     const int b = cand[c];
-    // one warm-up round, then two timed rounds; a shape the kernel cannot
-    // launch (too many registers for the block) is skipped
+    if (b > limit) continue;  // more registers than the SM gives one block
+    // one warm-up round, then two timed rounds
     bool ok = true;
     for (int rep = 0; rep < 3 && ok; ++rep) {
       if (rep == 1) cudaEventRecord(e0, L->stream);
@@ -445,6 +446,9 @@ int qcd_set_block(qcd_lattice* L, int threads) {
   if (int rc = check(L)) return rc;
   if (threads != 0 && (threads < 32 || threads > 1024 || threads % 32))
     return set_error(QCD_ERR_INVALID_ARG, "threads must be 0 or a multiple of 32 in [32, 1024]");
+  if (threads > L->ops->max_phase_block())
+    return set_error(QCD_ERR_INVALID_ARG, "the phase kernels launch with at most %d threads per block",
+                     L->ops->max_phase_block());
   L->block = threads;
   return QCD_OK;
 }

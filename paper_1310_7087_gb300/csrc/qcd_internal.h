@@ -53,6 +53,9 @@ struct PolicyOps {
   cudaError_t (*measure)(const Ctx&, int effective, cudaStream_t);
   cudaError_t (*to_canonical)(const Ctx&, double* dev_out, cudaStream_t);
   cudaError_t (*from_canonical)(const Ctx&, const double* dev_in, cudaStream_t);
+  // Largest block the phase kernels of this storage can launch with (the
+  // minimum over heat-bath / overrelaxation, with and without the field).
+  int (*max_phase_block)();
 };
 
 extern const PolicyOps kOpsSU2F64;

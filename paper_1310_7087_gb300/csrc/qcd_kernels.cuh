@@ -12,6 +12,8 @@
 //   SU(3) FP64  9 x double2  u_rc, r-major
 #pragma once
 
+#include <algorithm>
+
 #include "qcd_device.cuh"
 #include "qcd_internal.h"
 
@@ -724,6 +726,26 @@ cudaError_t launch_from_canonical(const Ctx& a, const double* in, cudaStream_t s
   return cudaGetLastError();
 }
 
+template <class P, bool FIELD, int KIND>
+int phase_block_limit() {
+  cudaFuncAttributes attr{};
+  cudaError_t e;
+  if constexpr (P::N == 2)
+    e = cudaFuncGetAttributes(&attr, su2_phase_kernel<typename P::Real, FIELD, KIND>);
+  else
+    e = cudaFuncGetAttributes(&attr, su3_phase_kernel<typename P::Real, FIELD, KIND>);
+  return e == cudaSuccess ? attr.maxThreadsPerBlock : 0;
+}
+
+template <class P>
+int max_phase_block() {
+  int m = phase_block_limit<P, false, KIND_HB>();
+  m = std::min(m, phase_block_limit<P, true, KIND_HB>());
+  m = std::min(m, phase_block_limit<P, false, KIND_OR>());
+  m = std::min(m, phase_block_limit<P, true, KIND_OR>());
+  return m;
+}
+
 template <class P>
 constexpr PolicyOps make_ops(int precision) {
   return PolicyOps{P::N,
@@ -734,7 +756,8 @@ constexpr PolicyOps make_ops(int precision) {
                    &launch_start<P>,
                    &launch_measure<P>,
                    &launch_to_canonical<P>,
-                   &launch_from_canonical<P>};
+                   &launch_from_canonical<P>,
+                   &max_phase_block<P>};
 }
 
 }  // namespace qcd
