@@ -162,6 +162,38 @@ int qcd_get_block(const qcd_lattice *lat, int *threads);
 int qcd_set_profiling(qcd_lattice *lat, int enable);
 int qcd_get_profile(qcd_lattice *lat, double *ms, unsigned long long *launches);
 
+/* Allocation-free measurement.  The paper has no counterpart: this entry point
+ * exists for callers that cannot let the library allocate device memory, such
+ * as code running inside a host framework that owns all device memory through
+ * its own pool (an extra cudaMalloc would fail under the pool's cap or
+ * synchronize the device mid-stream), or code that must have no allocation
+ * failure path.  It computes what qcd_measure computes, on link storage the
+ * caller already holds on the device, and calls no cudaMalloc, cudaFree or
+ * allocating library routine.
+ *   links      device pointer, the library's storage layout for (group,
+ *              precision, Ns, Nt): the bytes qcd_link_bytes reports and
+ *              qcd_copy_links_out produces.  Read only; owned by the caller.
+ *   flux       flux quantum of the background field (effective links U B).
+ *   plaquette  host double[3] {P, P_s, P_t} or NULL;
+ *   polyakov   host double[2] {Re L, Im L} or NULL.
+ *   stream     cudaStream_t or NULL; the call synchronizes it.
+ * Scratch: one file-scope device array of QCD_NOALLOC_SCRATCH_BYTES (512 KiB)
+ * per GPU that loads the library, held until the process exits.  A lattice
+ * needs 16 (ceil(V/256) + ceil(Ns^3/256)) bytes of block partials plus
+ * at most 24 Ns + 320 bytes; every lattice of at most 4,194,304 sites (such as
+ * 64^3 x 16) fits, a lattice that needs more returns QCD_ERR_INVALID_ARG with
+ * the sizes in qcd_last_error().  The
+ * first call on a device looks up the array's device address (with that device
+ * current); make that first call before any stream capture.  Every call on a
+ * device shares the array and overwrites what the previous call left there
+ * (nothing in it needs to start at zero), so calls that overlap on the GPU
+ * (different streams, or different host threads) race and must not be
+ * issued. */
+#define QCD_NOALLOC_SCRATCH_BYTES (512u * 1024u)
+int qcd_measure_noalloc(const void *links, int group, int precision, int Ns,
+                        int Nt, int flux, double *plaquette, double *polyakov,
+                        void *stream);
+
 /* Message of the last failed call on this thread ("" if none). */
 const char *qcd_last_error(void);
 

@@ -55,8 +55,10 @@ SIGNATURES = {
     "qcd_get_block": (_i, [_vp, _P(_i)]),
     "qcd_set_profiling": (_i, [_vp, _i]),
     "qcd_get_profile": (_i, [_vp, _P(_d), _P(ctypes.c_ulonglong)]),
+    "qcd_measure_noalloc": (_i, [_vp, _i, _i, _i, _i, _i, _P(_d), _P(_d), _vp]),
     "qcd_last_error": (ctypes.c_char_p, []),
 }
+QCD_NOALLOC_SCRATCH_BYTES = 512 * 1024
 QCD_PROF_HEATBATH, QCD_PROF_OVERRELAX, QCD_PROF_REUNIT, QCD_PROF_MEASURE = 0, 1, 2, 3
 QCD_PROF_N = 4
 
@@ -213,6 +215,18 @@ def qcd_get_profile(h):
     n = (ctypes.c_ulonglong * QCD_PROF_N)()
     _check(lib().qcd_get_profile(h, ms, n))
     return list(ms), list(n)
+
+
+def qcd_measure_noalloc(links_dev_ptr: int, group: int, precision: int, Ns: int, Nt: int,
+                        flux: int = 0, stream=None):
+    """Measurement that allocates nothing, on link storage the caller holds on
+    the device (``links_dev_ptr``, the layout qcd_copy_links_out produces).
+    Returns ([P, P_s, P_t], [Re L, Im L])."""
+    p = (ctypes.c_double * 3)()
+    l = (ctypes.c_double * 2)()
+    _check(lib().qcd_measure_noalloc(links_dev_ptr, group, precision, Ns, Nt, flux, p, l,
+                                     _stream_handle(stream)))
+    return list(p), list(l)
 
 
 def qcd_last_error() -> str:

@@ -353,6 +353,10 @@ int autotune(qcd_lattice* L) {
 
 }  // namespace
 
+namespace qcd {
+int set_last_error(int code, const char* msg) { return set_error(code, "%s", msg); }
+}  // namespace qcd
+
 extern "C" {
 
 const char* qcd_last_error(void) { return g_last_error.c_str(); }

@@ -58,6 +58,9 @@ struct PolicyOps {
   int (*max_phase_block)();
 };
 
+// Record the message returned by qcd_last_error() on this thread; returns code.
+int set_last_error(int code, const char* msg);
+
 extern const PolicyOps kOpsSU2F64;
 extern const PolicyOps kOpsSU2F32;
 extern const PolicyOps kOpsSU3F64;
