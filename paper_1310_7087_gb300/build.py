@@ -25,6 +25,12 @@ NVCC_FLAGS = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC",
                      "-I" + INCLUDE, "-I" + CSRC, "-Xptxas", "-v"]
 
 
+def extra_flags() -> list:
+    """Additional nvcc flags from QCD_NVCC_EXTRA (space separated), e.g. a
+    register cap for launch-shape experiments."""
+    return os.environ.get("QCD_NVCC_EXTRA", "").split()
+
+
 def nvcc() -> str:
     for cand in (shutil.which("nvcc"), "/usr/local/cuda/bin/nvcc"):
         if cand and os.path.exists(cand):
@@ -42,7 +48,7 @@ def _deps():
 
 
 def up_to_date() -> bool:
-    if not os.path.exists(LIB):
+    if not os.path.exists(LIB) or extra_flags():
         return False
     t = os.path.getmtime(LIB)
     return all(os.path.getmtime(p) <= t for p in _deps())
@@ -50,7 +56,7 @@ def up_to_date() -> bool:
 
 def _compile(src: str) -> tuple[str, str]:
     obj = os.path.join(BUILD, os.path.basename(src)[:-3] + ".o")
-    cmd = [nvcc(), *NVCC_FLAGS, "-c", src, "-o", obj]
+    cmd = [nvcc(), *NVCC_FLAGS, *extra_flags(), "-c", src, "-o", obj]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError("nvcc failed for %s:\n%s\n%s" % (src, r.stdout, r.stderr))

@@ -288,8 +288,14 @@ __device__ __forceinline__ void left_rotate(M3<R>& m, const Quat<R>& r, int i, i
   }
 }
 
+// Register cap of the SU(3) phase kernels: fewer registers per thread let more
+// warps stay resident to hide the latency of the 18-link gather.
+#ifndef QCD_SU3_PHASE_MAXNREG
+#define QCD_SU3_PHASE_MAXNREG 96
+#endif
+
 template <typename R, bool FIELD, int KIND>
-__global__ void su3_phase_kernel(const Ctx a, int parity, int mu) {
+__global__ void __maxnreg__(QCD_SU3_PHASE_MAXNREG) su3_phase_kernel(const Ctx a, int parity, int mu) {
   using P = SU3Policy<R>;
   const int h = blockIdx.x * blockDim.x + threadIdx.x;
   if (h >= a.g.Vh) return;
