@@ -355,6 +355,14 @@ __device__ __forceinline__ void advance_if(const Ctx& a, int advance) {
   if (advance && blockIdx.x == 0 && threadIdx.x == 0) *a.sweep_rw += 1u;
 }
 
+// 1 / sqrt(n) in FP64 for n near 1: an FP32 seed refined by one Newton step
+// y <- y (3 - n y^2) / 2 (relative error 2.4e-7 -> ~1e-13; FP64 storage takes
+// a second step).
+__device__ __forceinline__ double rsqrt_fp64(double n) {
+  const double y = double(rsqrtf(float(n)));
+  return y * fma(-0.5 * n, y * y, 1.5);
+}
+
 template <typename R>
 __global__ void su2_reunit_kernel(const Ctx a, int advance) {
   using P = SU2Policy<R>;
@@ -365,8 +373,34 @@ __global__ void su2_reunit_kernel(const Ctx a, int advance) {
   const int mu = plane >> 1, par = plane & 1;
   const Quat<R> u = P::load(a.links, a.g, mu, par, h);
   const double q0 = u.q0, q1 = u.q1, q2 = u.q2, q3 = u.q3;
-  const double inv = rsqrt(q0 * q0 + q1 * q1 + q2 * q2 + q3 * q3);
+  const double n = fma(q0, q0, fma(q1, q1, fma(q2, q2, q3 * q3)));
+  double inv = rsqrt_fp64(n);
+  if (sizeof(R) == 8) inv *= fma(-0.5 * n, inv * inv, 1.5);
   P::store(a.links, a.g, mu, par, h, Quat<R>{R(q0 * inv), R(q1 * inv), R(q2 * inv), R(q3 * inv)});
+}
+
+// Rows 0-1 of an SU(3) link in FP64 (FP32 storage holds exactly these).
+template <typename R>
+__device__ __forceinline__ void load_rows_fp64(const Ctx& a, int mu, int par, int h, Cx<double> r[2][3]) {
+  if constexpr (sizeof(R) == 4) {
+    const float4* p = reinterpret_cast<const float4*>(a.links);
+    const float4 x = __ldg(p + vidx(a.g, 0, mu, par, h));
+    const float4 y = __ldg(p + vidx(a.g, 1, mu, par, h));
+    const float4 z = __ldg(p + vidx(a.g, 2, mu, par, h));
+    r[0][0] = {x.x, x.y};
+    r[0][1] = {x.z, x.w};
+    r[0][2] = {y.x, y.y};
+    r[1][0] = {y.z, y.w};
+    r[1][1] = {z.x, z.y};
+    r[1][2] = {z.z, z.w};
+  } else {
+    const double2* p = reinterpret_cast<const double2*>(a.links);
+#pragma unroll
+    for (int k = 0; k < 6; ++k) {
+      const double2 v = __ldg(p + vidx(a.g, k, mu, par, h));
+      r[k / 3][k % 3] = {v.x, v.y};
+    }
+  }
 }
 
 template <typename R>
@@ -377,35 +411,41 @@ __global__ void su3_reunit_kernel(const Ctx a, int advance) {
   if (idx >= 8LL * a.g.Vh) return;
   const int plane = int(idx / a.g.Vh), h = int(idx % a.g.Vh);
   const int mu = plane >> 1, par = plane & 1;
-  const M3<R> u = P::load(a.links, a.g, mu, par, h);
   M3<double> d;
-#pragma unroll
-  for (int r = 0; r < 2; ++r)
-#pragma unroll
-    for (int c = 0; c < 3; ++c) d.e[r][c] = {double(u.e[r][c].re), double(u.e[r][c].im)};
+  load_rows_fp64<R>(a, mu, par, h, d.e);
+  // row 1 / |row 1|
   double n1 = 0.0;
 #pragma unroll
   for (int c = 0; c < 3; ++c) n1 = fma(d.e[0][c].re, d.e[0][c].re, fma(d.e[0][c].im, d.e[0][c].im, n1));
-  const double i1 = rsqrt(n1);
+  double i1 = rsqrt_fp64(n1);
+  if (sizeof(R) == 8) i1 *= fma(-0.5 * n1, i1 * i1, 1.5);
 #pragma unroll
   for (int c = 0; c < 3; ++c) d.e[0][c] = scale(d.e[0][c], i1);
+  // row 2 minus its projection on row 1, normalised
   Cx<double> proj{0.0, 0.0};
 #pragma unroll
   for (int c = 0; c < 3; ++c) proj = cfma_cn(d.e[0][c], d.e[1][c], proj);
 #pragma unroll
-  for (int c = 0; c < 3; ++c) d.e[1][c] = d.e[1][c] - proj * d.e[0][c];
+  for (int c = 0; c < 3; ++c)
+    d.e[1][c] = {fma(-proj.re, d.e[0][c].re, fma(proj.im, d.e[0][c].im, d.e[1][c].re)),
+                 fma(-proj.re, d.e[0][c].im, fma(-proj.im, d.e[0][c].re, d.e[1][c].im))};
   double n2 = 0.0;
 #pragma unroll
   for (int c = 0; c < 3; ++c) n2 = fma(d.e[1][c].re, d.e[1][c].re, fma(d.e[1][c].im, d.e[1][c].im, n2));
-  const double i2 = rsqrt(n2);
+  double i2 = rsqrt_fp64(n2);
+  if (sizeof(R) == 8) i2 *= fma(-0.5 * n2, i2 * i2, 1.5);
 #pragma unroll
   for (int c = 0; c < 3; ++c) d.e[1][c] = scale(d.e[1][c], i2);
-  m3_rebuild_row2(d);
   M3<R> out;
 #pragma unroll
-  for (int r = 0; r < 3; ++r)
+  for (int r = 0; r < 2; ++r)
 #pragma unroll
     for (int c = 0; c < 3; ++c) out.e[r][c] = {R(d.e[r][c].re), R(d.e[r][c].im)};
+  if constexpr (sizeof(R) == 8) {  // FP64 storage keeps row 3 = conj(row1 x row2)
+    m3_rebuild_row2(d);
+#pragma unroll
+    for (int c = 0; c < 3; ++c) out.e[2][c] = d.e[2][c];
+  }
   P::store(a.links, a.g, mu, par, h, out);
 }
 
