@@ -194,6 +194,51 @@ int qcd_measure_noalloc(const void *links, int group, int precision, int Ns,
                         int Nt, int flux, double *plaquette, double *polyakov,
                         void *stream);
 
+/* ------------------------------------------------------------------------
+ * Batched parameter scan.  The paper runs parameter scans as independent jobs
+ * handed out by its dispatcher (sec. 4; its fastest mode, sec. 5); here many
+ * independent SU(2) lattices of uneven sizes, each with its own beta and flux,
+ * are swept together by one persistent cooperative kernel launch captured in
+ * a CUDA graph.  Each lattice gets a group of CTAs in proportion to its
+ * volume and synchronises only within that group; waits are bounded.
+ * Lattice i uses Philox key (seed_lo ^ i * 0x9E3779B9, seed_hi): the same
+ * random numbers as a single lattice created with lattice_id i.
+ * ------------------------------------------------------------------------ */
+typedef struct qcd_batch qcd_batch;
+
+/* n lattices: Ns[i], Nt[i] even >= 2, beta[i] >= 0, flux[i]; group must be 2
+ * (QCD_ERR_NOT_SUPPORTED otherwise); precision and start as for
+ * qcd_lattice_create.  Arrays are host memory, read during the call. */
+int qcd_batch_create(qcd_batch **out, int n, int group, const int *Ns,
+                     const int *Nt, const double *beta, const int *flux,
+                     int precision, int start, uint64_t seed, void *stream);
+int qcd_batch_destroy(qcd_batch *b);
+
+/* n_sweeps sweeps of every lattice (each: 1 heat-bath pass, n_overrelax
+ * overrelaxation passes, FP64 reunitarization, measurement) in one launch.
+ * meas_out: host double[n][n_sweeps][5] = {P, P_s, P_t, Re L, Im L} after each
+ * sweep, or NULL.  The first call chooses the launch shape (autotune over 128,
+ * 256, 512 threads per CTA on a scratch copy).  Returns QCD_ERR_TIMEOUT if a
+ * group's barrier wait ran out (the sweep is then abandoned part-way).
+ * Synchronizes the stream. */
+int qcd_batch_sweep(qcd_batch *b, int n_sweeps, int n_overrelax, uint64_t seed,
+                    double *meas_out);
+/* Links of lattice `index` in the canonical FP64 host layout. */
+int qcd_batch_get_links(qcd_batch *b, int index, double *host_out);
+int qcd_batch_set_links(qcd_batch *b, int index, const double *host_in);
+int qcd_batch_get_sweep(qcd_batch *b, uint32_t *sweep);
+int qcd_batch_link_bytes(const qcd_batch *b, size_t *bytes);
+/* Launch shape: threads per CTA (0 = autotune, or 128 / 256 / 512) and the
+ * resulting number of CTAs. */
+int qcd_batch_set_block(qcd_batch *b, int threads);
+int qcd_batch_get_shape(qcd_batch *b, int *threads, int *ctas);
+/* Bound of every barrier wait, in seconds (default 2, at most 60). */
+int qcd_batch_set_wait(qcd_batch *b, double seconds);
+/* Test hook: lattice `lattice`'s barriers wait for one arrival that never
+ * comes, so the wait runs out and qcd_batch_sweep returns QCD_ERR_TIMEOUT;
+ * -1 switches it off. */
+int qcd_batch_inject_stall(qcd_batch *b, int lattice);
+
 /* Message of the last failed call on this thread ("" if none). */
 const char *qcd_last_error(void);
 

@@ -56,6 +56,17 @@ SIGNATURES = {
     "qcd_set_profiling": (_i, [_vp, _i]),
     "qcd_get_profile": (_i, [_vp, _P(_d), _P(ctypes.c_ulonglong)]),
     "qcd_measure_noalloc": (_i, [_vp, _i, _i, _i, _i, _i, _P(_d), _P(_d), _vp]),
+    "qcd_batch_create": (_i, [_P(_vp), _i, _i, _P(_i), _P(_i), _P(_d), _P(_i), _i, _i, _u64, _vp]),
+    "qcd_batch_destroy": (_i, [_vp]),
+    "qcd_batch_sweep": (_i, [_vp, _i, _i, _u64, _P(_d)]),
+    "qcd_batch_get_links": (_i, [_vp, _i, _P(_d)]),
+    "qcd_batch_set_links": (_i, [_vp, _i, _P(_d)]),
+    "qcd_batch_get_sweep": (_i, [_vp, _P(_u32)]),
+    "qcd_batch_link_bytes": (_i, [_vp, _P(_sz)]),
+    "qcd_batch_set_block": (_i, [_vp, _i]),
+    "qcd_batch_get_shape": (_i, [_vp, _P(_i), _P(_i)]),
+    "qcd_batch_set_wait": (_i, [_vp, _d]),
+    "qcd_batch_inject_stall": (_i, [_vp, _i]),
     "qcd_last_error": (ctypes.c_char_p, []),
 }
 QCD_NOALLOC_SCRATCH_BYTES = 512 * 1024
@@ -231,6 +242,107 @@ def qcd_measure_noalloc(links_dev_ptr: int, group: int, precision: int, Ns: int,
 
 def qcd_last_error() -> str:
     return lib().qcd_last_error().decode()
+
+
+def qcd_batch_create(group, Ns, Nt, beta, flux, precision=QCD_FP32_COMPRESSED, start=QCD_HOT,
+                     seed=1, stream=None) -> ctypes.c_void_p:
+    n = len(Ns)
+    h = ctypes.c_void_p()
+    ia = lambda v: (ctypes.c_int * n)(*[int(x) for x in v])
+    _check(lib().qcd_batch_create(ctypes.byref(h), n, group, ia(Ns), ia(Nt),
+                                  (ctypes.c_double * n)(*[float(x) for x in beta]), ia(flux),
+                                  precision, start, seed, _stream_handle(stream)))
+    return h
+
+
+def qcd_batch_destroy(h) -> None:
+    _check(lib().qcd_batch_destroy(h))
+
+
+def qcd_batch_sweep(h, n: int, n_sweeps: int, n_overrelax: int, seed: int, measure: bool = True):
+    """Returns the measurements as an (n, n_sweeps, 5) array (or None)."""
+    out = np.empty((n, n_sweeps, 5), np.float64) if measure else None
+    _check(lib().qcd_batch_sweep(h, n_sweeps, n_overrelax, seed, _dptr(out) if measure else None))
+    return out
+
+
+def qcd_batch_get_links(h, index: int, V: int) -> np.ndarray:
+    out = np.empty((V, 4, 2, 2, 2), np.float64)
+    _check(lib().qcd_batch_get_links(h, index, _dptr(out)))
+    return out[..., 0] + 1j * out[..., 1]
+
+
+def qcd_batch_set_links(h, index: int, links) -> None:
+    a = np.asarray(links)
+    if np.iscomplexobj(a):
+        a = np.stack([a.real, a.imag], axis=-1)
+    _check(lib().qcd_batch_set_links(h, index, _dptr(np.ascontiguousarray(a, dtype=np.float64))))
+
+
+def qcd_batch_get_sweep(h) -> int:
+    v = ctypes.c_uint32()
+    _check(lib().qcd_batch_get_sweep(h, ctypes.byref(v)))
+    return v.value
+
+
+def qcd_batch_link_bytes(h) -> int:
+    v = ctypes.c_size_t()
+    _check(lib().qcd_batch_link_bytes(h, ctypes.byref(v)))
+    return v.value
+
+
+def qcd_batch_set_block(h, threads: int) -> None:
+    _check(lib().qcd_batch_set_block(h, threads))
+
+
+def qcd_batch_get_shape(h):
+    t, c = ctypes.c_int(), ctypes.c_int()
+    _check(lib().qcd_batch_get_shape(h, ctypes.byref(t), ctypes.byref(c)))
+    return t.value, c.value
+
+
+def qcd_batch_set_wait(h, seconds: float) -> None:
+    _check(lib().qcd_batch_set_wait(h, seconds))
+
+
+def qcd_batch_inject_stall(h, lattice: int) -> None:
+    _check(lib().qcd_batch_inject_stall(h, lattice))
+
+
+class Batch:
+    """Owning wrapper around one ``qcd_batch`` handle (SU(2) lattices)."""
+
+    def __init__(self, Ns, Nt, beta, flux, precision=QCD_FP32_COMPRESSED, start=QCD_HOT, seed=1,
+                 stream=None):
+        self.Ns, self.Nt = list(Ns), list(Nt)
+        self.n = len(self.Ns)
+        self.V = [ns ** 3 * nt for ns, nt in zip(self.Ns, self.Nt)]
+        self.seed = seed
+        self.h = qcd_batch_create(2, Ns, Nt, beta, flux, precision, start, seed, stream)
+
+    def close(self):
+        if self.h:
+            qcd_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def sweep(self, n_sweeps=1, n_or=1, seed=None, measure=True):
+        return qcd_batch_sweep(self.h, self.n, n_sweeps, n_or, self.seed if seed is None else seed, measure)
+
+    def get_links(self, i):
+        return qcd_batch_get_links(self.h, i, self.V[i])
+
+    def set_links(self, i, links):
+        qcd_batch_set_links(self.h, i, links)
+
+    @property
+    def sweep_counter(self):
+        return qcd_batch_get_sweep(self.h)
 
 
 class Lattice:

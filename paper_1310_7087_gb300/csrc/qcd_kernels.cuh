@@ -20,8 +20,17 @@
 namespace qcd {
 
 // ---------------------------------------------------------------------------
-// Storage policies
+// Storage policies.  Loads go through the read-only path (ld.global.nc) when
+// the links cannot change while the kernel runs (one phase per launch); a
+// kernel that updates links between its own phases (the batched persistent
+// kernel) loads with CG = true (ld.global.cg: cached in L2 only, never a stale
+// L1 line).
 // ---------------------------------------------------------------------------
+template <bool CG, typename T>
+__device__ __forceinline__ T ld16(const T* p) {
+  if constexpr (CG) return __ldcg(p);
+  else return __ldg(p);
+}
 template <typename R>
 struct SU2Policy;
 
@@ -30,8 +39,9 @@ struct SU2Policy<float> {
   using Real = float;
   using Link = Quat<float>;
   static constexpr int N = 2, COMPS = 1;
+  template <bool CG = false>
   static __device__ __forceinline__ Link load(const void* base, const Geom& g, int mu, int par, int h) {
-    const float4 v = __ldg(reinterpret_cast<const float4*>(base) + vidx(g, 0, mu, par, h));
+    const float4 v = ld16<CG>(reinterpret_cast<const float4*>(base) + vidx(g, 0, mu, par, h));
     return {v.x, v.y, v.z, v.w};
   }
   static __device__ __forceinline__ void store(void* base, const Geom& g, int mu, int par, int h, const Link& u) {
@@ -44,9 +54,10 @@ struct SU2Policy<double> {
   using Real = double;
   using Link = Quat<double>;
   static constexpr int N = 2, COMPS = 2;
+  template <bool CG = false>
   static __device__ __forceinline__ Link load(const void* base, const Geom& g, int mu, int par, int h) {
     const double2* p = reinterpret_cast<const double2*>(base);
-    const double2 a = __ldg(p + vidx(g, 0, mu, par, h)), b = __ldg(p + vidx(g, 1, mu, par, h));
+    const double2 a = ld16<CG>(p + vidx(g, 0, mu, par, h)), b = ld16<CG>(p + vidx(g, 1, mu, par, h));
     return {a.x, a.y, b.x, b.y};
   }
   static __device__ __forceinline__ void store(void* base, const Geom& g, int mu, int par, int h, const Link& u) {
@@ -64,11 +75,12 @@ struct SU3Policy<float> {
   using Real = float;
   using Link = M3<float>;
   static constexpr int N = 3, COMPS = 3;
+  template <bool CG = false>
   static __device__ __forceinline__ Link load(const void* base, const Geom& g, int mu, int par, int h) {
     const float4* p = reinterpret_cast<const float4*>(base);
-    const float4 a = __ldg(p + vidx(g, 0, mu, par, h));
-    const float4 b = __ldg(p + vidx(g, 1, mu, par, h));
-    const float4 c = __ldg(p + vidx(g, 2, mu, par, h));
+    const float4 a = ld16<CG>(p + vidx(g, 0, mu, par, h));
+    const float4 b = ld16<CG>(p + vidx(g, 1, mu, par, h));
+    const float4 c = ld16<CG>(p + vidx(g, 2, mu, par, h));
     Link m;
     m.e[0][0] = {a.x, a.y};
     m.e[0][1] = {a.z, a.w};
@@ -92,12 +104,13 @@ struct SU3Policy<double> {
   using Real = double;
   using Link = M3<double>;
   static constexpr int N = 3, COMPS = 9;
+  template <bool CG = false>
   static __device__ __forceinline__ Link load(const void* base, const Geom& g, int mu, int par, int h) {
     const double2* p = reinterpret_cast<const double2*>(base);
     Link m;
 #pragma unroll
     for (int k = 0; k < 9; ++k) {
-      const double2 v = __ldg(p + vidx(g, k, mu, par, h));
+      const double2 v = ld16<CG>(p + vidx(g, k, mu, par, h));
       m.e[k / 3][k % 3] = {v.x, v.y};
     }
     return m;
@@ -175,10 +188,10 @@ __device__ __forceinline__ void load_phase<double>(const Ctx& a, int x, double& 
 }
 
 // Effective link Ut_mu(site) = U_mu(site) B_mu(site).
-template <class P, bool FIELD>
+template <class P, bool FIELD, bool CG = false>
 __device__ __forceinline__ typename P::Link load_eff(const Ctx& a, int mu, const Site& c) {
   using R = typename P::Real;
-  typename P::Link u = P::load(a.links, a.g, mu, parity_of(c), lex(a.g, c) >> 1);
+  typename P::Link u = P::template load<CG>(a.links, a.g, mu, parity_of(c), lex(a.g, c) >> 1);
   if (FIELD && mu == 1) {
     R ph_c, ph_s;
     load_phase<R>(a, c.x, ph_c, ph_s);
@@ -190,7 +203,7 @@ __device__ __forceinline__ typename P::Link load_eff(const Ctx& a, int mu, const
 // Staple sum of U_mu(x) on effective links:
 //   A = sum_{nu != mu} Ut_nu(x+mu) Ut_mu(x+nu)^+ Ut_nu(x)^+
 //                    + (Ut_mu(x-nu) Ut_nu(x+mu-nu))^+ Ut_nu(x-nu)
-template <class P, bool FIELD>
+template <class P, bool FIELD, bool CG = false>
 __device__ __forceinline__ typename P::Link staple(const Ctx& a, const Site& x, int mu) {
   using R = typename P::Real;
   using A = Alg<R>;
@@ -204,15 +217,15 @@ __device__ __forceinline__ typename P::Link staple(const Ctx& a, const Site& x, 
     const Site xmn = step(a.g, x, nu, -1);
     const Site xpmn = step(a.g, xp, nu, -1);
     {
-      const auto u1 = load_eff<P, FIELD>(a, nu, xp);
-      const auto u2 = load_eff<P, FIELD>(a, mu, xpn);
-      const auto u3 = load_eff<P, FIELD>(a, nu, x);
+      const auto u1 = load_eff<P, FIELD, CG>(a, nu, xp);
+      const auto u2 = load_eff<P, FIELD, CG>(a, mu, xpn);
+      const auto u3 = load_eff<P, FIELD, CG>(a, nu, x);
       A::acc_nd(acc, A::mul_nd(u1, u2), u3);
     }
     {
-      const auto l1 = load_eff<P, FIELD>(a, nu, xpmn);
-      const auto l2 = load_eff<P, FIELD>(a, mu, xmn);
-      const auto l3 = load_eff<P, FIELD>(a, nu, xmn);
+      const auto l1 = load_eff<P, FIELD, CG>(a, nu, xpmn);
+      const auto l2 = load_eff<P, FIELD, CG>(a, mu, xmn);
+      const auto l3 = load_eff<P, FIELD, CG>(a, nu, xmn);
       A::acc_dn(acc, A::mul(l2, l1), l3);
     }
   }
@@ -223,13 +236,11 @@ __device__ __forceinline__ typename P::Link staple(const Ctx& a, const Site& x, 
 // SU(2) phase update: Kennedy-Pendleton heat-bath or overrelaxation of the
 // links of direction mu on sites of one parity.
 // ---------------------------------------------------------------------------
-template <typename R, bool FIELD, int KIND>
-__global__ void su2_phase_kernel(const Ctx a, int parity, int mu) {
+template <typename R, bool FIELD, int KIND, bool CG = false>
+__device__ __forceinline__ void su2_update_site(const Ctx& a, int parity, int mu, int h, uint32_t sweep) {
   using P = SU2Policy<R>;
-  const int h = blockIdx.x * blockDim.x + threadIdx.x;
-  if (h >= a.g.Vh) return;
   const Site x = site_of(a.g, parity, h);
-  const Quat<R> A = staple<P, FIELD>(a, x, mu);
+  const Quat<R> A = staple<P, FIELD, CG>(a, x, mu);
   const R k = q_sqrt(qnorm2(A));  // sqrt(det A)
   const bool phased = FIELD && mu == 1;
   R bc = R(1), bs = R(0);
@@ -240,7 +251,6 @@ __global__ void su2_phase_kernel(const Ctx a, int parity, int mu) {
   if (KIND == KIND_HB) {
     const R alpha = R(a.beta) * k;
     const uint32_t s = uint32_t(lex(a.g, x));
-    const uint32_t sweep = *a.sweep;
     const Stream dir = make_stream(a.k0, a.k1, s, sweep, mu, 0, KIND_DIR);
     if (alpha == R(0)) {
       ut_new = su2_haar<R>(dir, 0u);
@@ -258,12 +268,19 @@ __global__ void su2_phase_kernel(const Ctx a, int parity, int mu) {
   } else {
     if (k == R(0)) return;
     const Quat<R> Vd = qdag(qscale(A, R(1) / k));
-    Quat<R> ut = P::load(a.links, a.g, mu, parity, h);
+    Quat<R> ut = P::template load<CG>(a.links, a.g, mu, parity, h);
     if (phased) ut = qmul(ut, qdag(Bd));
     ut_new = qmul(qmul(Vd, qdag(ut)), Vd);
   }
   const Quat<R> u_new = phased ? qmul(ut_new, Bd) : ut_new;
   P::store(a.links, a.g, mu, parity, h, u_new);
+}
+
+template <typename R, bool FIELD, int KIND>
+__global__ void su2_phase_kernel(const Ctx a, int parity, int mu) {
+  const int h = blockIdx.x * blockDim.x + threadIdx.x;
+  if (h >= a.g.Vh) return;
+  su2_update_site<R, FIELD, KIND>(a, parity, mu, h, KIND == KIND_HB ? *a.sweep : 0u);
 }
 
 // ---------------------------------------------------------------------------
@@ -363,20 +380,24 @@ __device__ __forceinline__ double rsqrt_fp64(double n) {
   return y * fma(-0.5 * n, y * y, 1.5);
 }
 
-template <typename R>
-__global__ void su2_reunit_kernel(const Ctx a, int advance) {
+template <typename R, bool CG = false>
+__device__ __forceinline__ void su2_reunit_link(const Ctx& a, int mu, int par, int h) {
   using P = SU2Policy<R>;
-  advance_if(a, advance);
-  const int64_t idx = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
-  if (idx >= 8LL * a.g.Vh) return;
-  const int plane = int(idx / a.g.Vh), h = int(idx % a.g.Vh);
-  const int mu = plane >> 1, par = plane & 1;
-  const Quat<R> u = P::load(a.links, a.g, mu, par, h);
+  const Quat<R> u = P::template load<CG>(a.links, a.g, mu, par, h);
   const double q0 = u.q0, q1 = u.q1, q2 = u.q2, q3 = u.q3;
   const double n = fma(q0, q0, fma(q1, q1, fma(q2, q2, q3 * q3)));
   double inv = rsqrt_fp64(n);
   if (sizeof(R) == 8) inv *= fma(-0.5 * n, inv * inv, 1.5);
   P::store(a.links, a.g, mu, par, h, Quat<R>{R(q0 * inv), R(q1 * inv), R(q2 * inv), R(q3 * inv)});
+}
+
+template <typename R>
+__global__ void su2_reunit_kernel(const Ctx a, int advance) {
+  advance_if(a, advance);
+  const int64_t idx = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (idx >= 8LL * a.g.Vh) return;
+  const int plane = int(idx / a.g.Vh), h = int(idx % a.g.Vh);
+  su2_reunit_link<R>(a, plane >> 1, plane & 1, h);
 }
 
 // Rows 0-1 of an SU(3) link in FP64 (FP32 storage holds exactly these).
@@ -556,52 +577,62 @@ __device__ __forceinline__ void block_sum2(double& v0, double& v1, double* parti
   }
 }
 
-template <class P, bool FIELD>
-__global__ void __launch_bounds__(MEAS_THREADS) measure_kernel(const Ctx a, int n_plaq_blocks) {
+// Plaquettes of one site (index idx over both parities): spatial sum into v0,
+// temporal sum into v1, (1/N) Re Tr each, FP64.
+template <class P, bool FIELD, bool CG = false>
+__device__ __forceinline__ void plaquette_site(const Ctx& a, int64_t idx, double& v0, double& v1) {
   using R = typename P::Real;
   using A = Alg<R>;
+  const int par = int(idx / a.g.Vh), h = int(idx % a.g.Vh);
+  const Site x = site_of(a.g, par, h);
+#pragma unroll
+  for (int mu = 0; mu < 4; ++mu) {
+    const Site xpm = step(a.g, x, mu, +1);
+    const auto umu = load_eff<P, FIELD, CG>(a, mu, x);
+#pragma unroll
+    for (int nu = mu + 1; nu < 4; ++nu) {
+      const Site xpn = step(a.g, x, nu, +1);
+      const auto ab = A::mul(umu, load_eff<P, FIELD, CG>(a, nu, xpm));
+      const auto dc = A::mul(load_eff<P, FIELD, CG>(a, nu, x), load_eff<P, FIELD, CG>(a, mu, xpn));
+      const double p = double(A::retr_nd_over_n(ab, dc));
+      if (nu == 3) v1 += p;
+      else v0 += p;
+    }
+  }
+}
+
+// Polyakov loop of spatial site idx: (1/N) Tr of the ordered t-product, FP64.
+template <class P, bool CG = false>
+__device__ __forceinline__ void polyakov_site(const Ctx& a, int64_t idx, double& v0, double& v1) {
+  using R = typename P::Real;
+  using A = Alg<R>;
+  Site x;
+  x.x = int(idx % a.g.Ns);
+  x.y = int((idx / a.g.Ns) % a.g.Ns);
+  x.z = int(idx / (int64_t(a.g.Ns) * a.g.Ns));
+  x.t = 0;
+  auto l = P::template load<CG>(a.links, a.g, 3, parity_of(x), lex(a.g, x) >> 1);
+  for (int t = 1; t < a.g.Nt; ++t) {
+    x.t = t;
+    l = A::mul(l, P::template load<CG>(a.links, a.g, 3, parity_of(x), lex(a.g, x) >> 1));
+  }
+  if constexpr (P::N == 2) {
+    v0 += double(l.q0);
+  } else {
+    v0 += (double(l.e[0][0].re) + double(l.e[1][1].re) + double(l.e[2][2].re)) / 3.0;
+    v1 += (double(l.e[0][0].im) + double(l.e[1][1].im) + double(l.e[2][2].im)) / 3.0;
+  }
+}
+
+template <class P, bool FIELD>
+__global__ void __launch_bounds__(MEAS_THREADS) measure_kernel(const Ctx a, int n_plaq_blocks) {
   double v0 = 0.0, v1 = 0.0;
   if (int(blockIdx.x) < n_plaq_blocks) {
     const int64_t idx = int64_t(blockIdx.x) * MEAS_THREADS + threadIdx.x;
-    if (idx < 2LL * a.g.Vh) {
-      const int par = int(idx / a.g.Vh), h = int(idx % a.g.Vh);
-      const Site x = site_of(a.g, par, h);
-#pragma unroll
-      for (int mu = 0; mu < 4; ++mu) {
-        const Site xpm = step(a.g, x, mu, +1);
-        const auto umu = load_eff<P, FIELD>(a, mu, x);
-#pragma unroll
-        for (int nu = mu + 1; nu < 4; ++nu) {
-          const Site xpn = step(a.g, x, nu, +1);
-          const auto ab = A::mul(umu, load_eff<P, FIELD>(a, nu, xpm));
-          const auto dc = A::mul(load_eff<P, FIELD>(a, nu, x), load_eff<P, FIELD>(a, mu, xpn));
-          const double p = double(A::retr_nd_over_n(ab, dc));
-          if (nu == 3) v1 += p;
-          else v0 += p;
-        }
-      }
-    }
+    if (idx < 2LL * a.g.Vh) plaquette_site<P, FIELD>(a, idx, v0, v1);
   } else {
     const int64_t idx = int64_t(int(blockIdx.x) - n_plaq_blocks) * MEAS_THREADS + threadIdx.x;
-    const int64_t V3 = int64_t(a.g.Ns) * a.g.Ns * a.g.Ns;
-    if (idx < V3) {
-      Site x;
-      x.x = int(idx % a.g.Ns);
-      x.y = int((idx / a.g.Ns) % a.g.Ns);
-      x.z = int(idx / (int64_t(a.g.Ns) * a.g.Ns));
-      x.t = 0;
-      auto l = P::load(a.links, a.g, 3, parity_of(x), lex(a.g, x) >> 1);
-      for (int t = 1; t < a.g.Nt; ++t) {
-        x.t = t;
-        l = A::mul(l, P::load(a.links, a.g, 3, parity_of(x), lex(a.g, x) >> 1));
-      }
-      if constexpr (P::N == 2) {
-        v0 = double(l.q0);
-      } else {
-        v0 = (double(l.e[0][0].re) + double(l.e[1][1].re) + double(l.e[2][2].re)) / 3.0;
-        v1 = (double(l.e[0][0].im) + double(l.e[1][1].im) + double(l.e[2][2].im)) / 3.0;
-      }
-    }
+    if (idx < int64_t(a.g.Ns) * a.g.Ns * a.g.Ns) polyakov_site<P>(a, idx, v0, v1);
   }
   block_sum2(v0, v1, a.partials + 2 * blockIdx.x);
 }
