@@ -380,15 +380,53 @@ __device__ __forceinline__ double rsqrt_fp64(double n) {
   return y * fma(-0.5 * n, y * y, 1.5);
 }
 
+// Exact dot products of FP32 vectors, finished in FP64 (Ogita, Rump & Oishi,
+// "Accurate sum and dot product", SIAM J. Sci. Comput. 26 (2005), Dot2):
+// every product x*y is split exactly into p + e with p = fl(x*y) and
+// e = fma(x, y, -p); the p's are summed with Knuth's error-free TwoSum, the
+// rounding errors collected, and the two FP32 parts are added in FP64.  The
+// result carries ~2^-46 relative error, the same as an FP64 accumulation of
+// the (exactly representable) FP64 products, with two FP32->FP64 conversions
+// instead of one per input.
+struct Dot2 {
+  float s = 0.f, c = 0.f;
+  __device__ __forceinline__ void add(float x, float y) {
+    const float p = x * y;
+    const float e = fmaf(x, y, -p);
+    const float t = s + p;
+    const float bp = t - s;
+    const float err = (s - (t - bp)) + (p - bp);
+    s = t;
+    c += err + e;
+  }
+  __device__ __forceinline__ double value() const { return double(s) + double(c); }
+};
+
+// u * (1 + d) rounded once: u + d u with d small.
+__device__ __forceinline__ float scale1p(float u, float d) { return fmaf(d, u, u); }
+
 template <typename R, bool CG = false>
 __device__ __forceinline__ void su2_reunit_link(const Ctx& a, int mu, int par, int h) {
   using P = SU2Policy<R>;
   const Quat<R> u = P::template load<CG>(a.links, a.g, mu, par, h);
-  const double q0 = u.q0, q1 = u.q1, q2 = u.q2, q3 = u.q3;
-  const double n = fma(q0, q0, fma(q1, q1, fma(q2, q2, q3 * q3)));
-  double inv = rsqrt_fp64(n);
-  if (sizeof(R) == 8) inv *= fma(-0.5 * n, inv * inv, 1.5);
-  P::store(a.links, a.g, mu, par, h, Quat<R>{R(q0 * inv), R(q1 * inv), R(q2 * inv), R(q3 * inv)});
+  if constexpr (sizeof(R) == 4) {
+    // |q|^2 exactly, 1/|q| in FP64, q (1 + (1/|q| - 1)) rounded once in FP32
+    Dot2 n;
+    n.add(u.q0, u.q0);
+    n.add(u.q1, u.q1);
+    n.add(u.q2, u.q2);
+    n.add(u.q3, u.q3);
+    const double nn = n.value();
+    const float d = float(rsqrt_fp64(nn) - 1.0);
+    P::store(a.links, a.g, mu, par, h,
+             Quat<R>{scale1p(u.q0, d), scale1p(u.q1, d), scale1p(u.q2, d), scale1p(u.q3, d)});
+  } else {
+    const double q0 = u.q0, q1 = u.q1, q2 = u.q2, q3 = u.q3;
+    const double nn = fma(q0, q0, fma(q1, q1, fma(q2, q2, q3 * q3)));
+    double inv = rsqrt_fp64(nn);
+    inv *= fma(-0.5 * nn, inv * inv, 1.5);
+    P::store(a.links, a.g, mu, par, h, Quat<R>{q0 * inv, q1 * inv, q2 * inv, q3 * inv});
+  }
 }
 
 template <typename R>
@@ -400,74 +438,107 @@ __global__ void su2_reunit_kernel(const Ctx a, int advance) {
   su2_reunit_link<R>(a, plane >> 1, plane & 1, h);
 }
 
-// Rows 0-1 of an SU(3) link in FP64 (FP32 storage holds exactly these).
-template <typename R>
+// SU(3), FP32 storage (rows 1-2).  Gram-Schmidt written through three exact
+// FP64 quantities of the stored rows r, t:
+//   n1 = |r|^2,  c = <r, t> = sum conj(r_k) t_k,  m = |t|^2,
+//   s1 = 1/sqrt(n1),  q = c / n1,  n2 = |t - q r|^2 = m - |c|^2 / n1,
+//   s2 = 1/sqrt(n2),
+//   row 1 = s1 r,  row 2 = s2 (t - q r) = t + ((s2 - 1) t - s2 q r),
+// all scalars in FP64; each output element is its input plus an FP64-derived
+// small correction, so it is rounded once, as an FP64 result stored in FP32.
+__device__ __forceinline__ void su3f_reunit_rows(Cx<float> r[3], Cx<float> t[3]) {
+  Dot2 n1, m, cre, cim;
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    n1.add(r[k].re, r[k].re);
+    n1.add(r[k].im, r[k].im);
+    m.add(t[k].re, t[k].re);
+    m.add(t[k].im, t[k].im);
+    cre.add(r[k].re, t[k].re);  // Re conj(r) t = r.re t.re + r.im t.im
+    cre.add(r[k].im, t[k].im);
+    cim.add(r[k].re, t[k].im);  // Im conj(r) t = r.re t.im - r.im t.re
+    cim.add(-r[k].im, t[k].re);
+  }
+  const double N1 = n1.value(), M = m.value(), Cre = cre.value(), Cim = cim.value();
+  const double s1 = rsqrt_fp64(N1);
+  const double inv_n1 = s1 * s1;
+  const double qre = Cre * inv_n1, qim = Cim * inv_n1;
+  const double n2 = M - fma(Cre, qre, Cim * qim);
+  const double s2 = rsqrt_fp64(n2);
+  const float d1 = float(s1 - 1.0), d2 = float(s2 - 1.0);
+  const float bre = float(s2 * qre), bim = float(s2 * qim);  // s2 q
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    // row 2: t + (d2 t - b r), b = s2 q (complex)
+    const float cre_k = fmaf(d2, t[k].re, -fmaf(bre, r[k].re, -bim * r[k].im));
+    const float cim_k = fmaf(d2, t[k].im, -fmaf(bre, r[k].im, bim * r[k].re));
+    t[k] = {t[k].re + cre_k, t[k].im + cim_k};
+    r[k] = {scale1p(r[k].re, d1), scale1p(r[k].im, d1)};
+  }
+}
+
+// Rows 0-1 of an SU(3) link in FP64 storage.
+template <bool CG>
 __device__ __forceinline__ void load_rows_fp64(const Ctx& a, int mu, int par, int h, Cx<double> r[2][3]) {
+  const double2* p = reinterpret_cast<const double2*>(a.links);
+#pragma unroll
+  for (int k = 0; k < 6; ++k) {
+    const double2 v = ld16<CG>(p + vidx(a.g, k, mu, par, h));
+    r[k / 3][k % 3] = {v.x, v.y};
+  }
+}
+
+template <typename R, bool CG = false>
+__device__ __forceinline__ void su3_reunit_link(const Ctx& a, int mu, int par, int h) {
+  using P = SU3Policy<R>;
   if constexpr (sizeof(R) == 4) {
     const float4* p = reinterpret_cast<const float4*>(a.links);
-    const float4 x = __ldg(p + vidx(a.g, 0, mu, par, h));
-    const float4 y = __ldg(p + vidx(a.g, 1, mu, par, h));
-    const float4 z = __ldg(p + vidx(a.g, 2, mu, par, h));
-    r[0][0] = {x.x, x.y};
-    r[0][1] = {x.z, x.w};
-    r[0][2] = {y.x, y.y};
-    r[1][0] = {y.z, y.w};
-    r[1][1] = {z.x, z.y};
-    r[1][2] = {z.z, z.w};
+    const float4 x = ld16<CG>(p + vidx(a.g, 0, mu, par, h));
+    const float4 y = ld16<CG>(p + vidx(a.g, 1, mu, par, h));
+    const float4 z = ld16<CG>(p + vidx(a.g, 2, mu, par, h));
+    Cx<float> r[3] = {{x.x, x.y}, {x.z, x.w}, {y.x, y.y}};
+    Cx<float> t[3] = {{y.z, y.w}, {z.x, z.y}, {z.z, z.w}};
+    su3f_reunit_rows(r, t);
+    float4* q = reinterpret_cast<float4*>(a.links);
+    q[vidx(a.g, 0, mu, par, h)] = make_float4(r[0].re, r[0].im, r[1].re, r[1].im);
+    q[vidx(a.g, 1, mu, par, h)] = make_float4(r[2].re, r[2].im, t[0].re, t[0].im);
+    q[vidx(a.g, 2, mu, par, h)] = make_float4(t[1].re, t[1].im, t[2].re, t[2].im);
   } else {
-    const double2* p = reinterpret_cast<const double2*>(a.links);
+    M3<double> d;
+    load_rows_fp64<CG>(a, mu, par, h, d.e);
+    double n1 = 0.0;
 #pragma unroll
-    for (int k = 0; k < 6; ++k) {
-      const double2 v = __ldg(p + vidx(a.g, k, mu, par, h));
-      r[k / 3][k % 3] = {v.x, v.y};
-    }
+    for (int c = 0; c < 3; ++c) n1 = fma(d.e[0][c].re, d.e[0][c].re, fma(d.e[0][c].im, d.e[0][c].im, n1));
+    double i1 = rsqrt_fp64(n1);
+    i1 *= fma(-0.5 * n1, i1 * i1, 1.5);
+#pragma unroll
+    for (int c = 0; c < 3; ++c) d.e[0][c] = scale(d.e[0][c], i1);
+    Cx<double> proj{0.0, 0.0};
+#pragma unroll
+    for (int c = 0; c < 3; ++c) proj = cfma_cn(d.e[0][c], d.e[1][c], proj);
+#pragma unroll
+    for (int c = 0; c < 3; ++c)
+      d.e[1][c] = {fma(-proj.re, d.e[0][c].re, fma(proj.im, d.e[0][c].im, d.e[1][c].re)),
+                   fma(-proj.re, d.e[0][c].im, fma(-proj.im, d.e[0][c].re, d.e[1][c].im))};
+    double n2 = 0.0;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) n2 = fma(d.e[1][c].re, d.e[1][c].re, fma(d.e[1][c].im, d.e[1][c].im, n2));
+    double i2 = rsqrt_fp64(n2);
+    i2 *= fma(-0.5 * n2, i2 * i2, 1.5);
+#pragma unroll
+    for (int c = 0; c < 3; ++c) d.e[1][c] = scale(d.e[1][c], i2);
+    m3_rebuild_row2(d);
+    P::store(a.links, a.g, mu, par, h, d);
   }
 }
 
 template <typename R>
 __global__ void su3_reunit_kernel(const Ctx a, int advance) {
-  using P = SU3Policy<R>;
   advance_if(a, advance);
   const int64_t idx = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
   if (idx >= 8LL * a.g.Vh) return;
   const int plane = int(idx / a.g.Vh), h = int(idx % a.g.Vh);
-  const int mu = plane >> 1, par = plane & 1;
-  M3<double> d;
-  load_rows_fp64<R>(a, mu, par, h, d.e);
-  // row 1 / |row 1|
-  double n1 = 0.0;
-#pragma unroll
-  for (int c = 0; c < 3; ++c) n1 = fma(d.e[0][c].re, d.e[0][c].re, fma(d.e[0][c].im, d.e[0][c].im, n1));
-  double i1 = rsqrt_fp64(n1);
-  if (sizeof(R) == 8) i1 *= fma(-0.5 * n1, i1 * i1, 1.5);
-#pragma unroll
-  for (int c = 0; c < 3; ++c) d.e[0][c] = scale(d.e[0][c], i1);
-  // row 2 minus its projection on row 1, normalised
-  Cx<double> proj{0.0, 0.0};
-#pragma unroll
-  for (int c = 0; c < 3; ++c) proj = cfma_cn(d.e[0][c], d.e[1][c], proj);
-#pragma unroll
-  for (int c = 0; c < 3; ++c)
-    d.e[1][c] = {fma(-proj.re, d.e[0][c].re, fma(proj.im, d.e[0][c].im, d.e[1][c].re)),
-                 fma(-proj.re, d.e[0][c].im, fma(-proj.im, d.e[0][c].re, d.e[1][c].im))};
-  double n2 = 0.0;
-#pragma unroll
-  for (int c = 0; c < 3; ++c) n2 = fma(d.e[1][c].re, d.e[1][c].re, fma(d.e[1][c].im, d.e[1][c].im, n2));
-  double i2 = rsqrt_fp64(n2);
-  if (sizeof(R) == 8) i2 *= fma(-0.5 * n2, i2 * i2, 1.5);
-#pragma unroll
-  for (int c = 0; c < 3; ++c) d.e[1][c] = scale(d.e[1][c], i2);
-  M3<R> out;
-#pragma unroll
-  for (int r = 0; r < 2; ++r)
-#pragma unroll
-    for (int c = 0; c < 3; ++c) out.e[r][c] = {R(d.e[r][c].re), R(d.e[r][c].im)};
-  if constexpr (sizeof(R) == 8) {  // FP64 storage keeps row 3 = conj(row1 x row2)
-    m3_rebuild_row2(d);
-#pragma unroll
-    for (int c = 0; c < 3; ++c) out.e[2][c] = d.e[2][c];
-  }
-  P::store(a.links, a.g, mu, par, h, out);
+  su3_reunit_link<R>(a, plane >> 1, plane & 1, h);
 }
 
 // ---------------------------------------------------------------------------

@@ -273,3 +273,28 @@ def test_ensemble_su2_4x4(q, precision):
         (ma, ea), (mb, eb) = binned(a), binned(b)
         assert abs(ma - mb) < 3 * np.hypot(ea, eb) + 1e-12, (ma, ea, mb, eb)
     lat.close()
+
+
+@pytest.mark.parametrize("group", [2, 3])
+@pytest.mark.parametrize("precision", [FP64_PLAIN, FP32_COMPRESSED])
+def test_reunitarization_of_perturbed_links(q, group, precision):
+    """Links pushed 1e-3 off the group: the GPU's reunitarization matches the
+    oracle's FP64 Gram-Schmidt of the same stored values to rounding (FP32
+    storage: about one unit in the last place) and restores unitarity."""
+    lat = q.Lattice(group, 4, 4, 2.0, 0, precision, HOT, 13)
+    U = lat.get_links()
+    rng = np.random.default_rng(1)
+    P = U + 1e-3 * (rng.normal(size=U.shape) + 1j * rng.normal(size=U.shape))
+    lat.set_links(P)
+    stored = lat.get_links()  # what the storage keeps (FP32 rows, SU(2) projection)
+    orc = oracle.OracleLattice(group, 4, 4, 2.0, 0, 10, 0)
+    orc.set_links(stored)
+    lat.reunitarize()
+    orc.reunitarize()
+    got, ref = lat.get_links(), orc.get_links()
+    tol = 1e-14 if precision == FP64_PLAIN else 2.5e-7
+    assert link_err(got, ref).max() < tol
+    M = got.reshape(-1, group, group)
+    unit = np.abs(np.einsum("nki,nkj->nij", M.conj(), M) - np.eye(group)).max()
+    assert unit < (1e-14 if precision == FP64_PLAIN else 5e-7)
+    lat.close()
