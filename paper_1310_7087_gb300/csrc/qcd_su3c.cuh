@@ -16,6 +16,13 @@
 
 #include "qcd_kernels.cuh"
 
+// Issue L2 prefetches for all gathered links before the staple (more memory
+// requests in flight without holding registers).
+#ifndef QCD_SU3C_PREFETCH
+#define QCD_SU3C_PREFETCH 0
+#endif
+
+
 namespace qcd {
 
 // Rows 0 and 1 of an SU(3) matrix.
@@ -157,6 +164,45 @@ __device__ __forceinline__ Rows2 su3c_eff(const Ctx& a, int par, const LexSite& 
   return r;
 }
 
+// Ask L2 for the three 16-byte vectors of link (D, par, site) ahead of use.
+template <int D>
+__device__ __forceinline__ void su3c_prefetch(const Ctx& a, int par, const LexSite& x) {
+  const float4* p = reinterpret_cast<const float4*>(a.links);
+#pragma unroll
+  for (int c = 0; c < 3; ++c)
+    asm volatile("prefetch.global.L2 [%0];" ::"l"(p + vidx(a.g, c, D, par, x.s >> 1)));
+}
+
+// All 18 gathered links of U_MU(x) and the link itself.
+template <int MU>
+__device__ __forceinline__ void su3c_prefetch_all(const Ctx& a, int p, const LexSite& x) {
+  const LexSite xp = su3c_step<MU, +1>(a.g, x);
+  su3c_prefetch<MU>(a, p, x);
+#pragma unroll
+  for (int nu = 0; nu < 4; ++nu) {
+    if (nu == MU) continue;
+    switch (nu) {
+#define QCD_SU3C_PF(NU)                                             \
+  case NU: {                                                        \
+    const LexSite xpn = su3c_step<NU, +1>(a.g, x);                  \
+    const LexSite xmn = su3c_step<NU, -1>(a.g, x);                  \
+    su3c_prefetch<NU>(a, p ^ 1, xp);                                \
+    su3c_prefetch<MU>(a, p ^ 1, xpn);                               \
+    su3c_prefetch<NU>(a, p, x);                                     \
+    su3c_prefetch<MU>(a, p ^ 1, xmn);                               \
+    su3c_prefetch<NU>(a, p, su3c_step<NU, -1>(a.g, xp));            \
+    su3c_prefetch<NU>(a, p ^ 1, xmn);                               \
+    break;                                                          \
+  }
+      QCD_SU3C_PF(0)
+      QCD_SU3C_PF(1)
+      QCD_SU3C_PF(2)
+      QCD_SU3C_PF(3)
+#undef QCD_SU3C_PF
+    }
+  }
+}
+
 // Staple sum of U_MU(x) (x of parity p) on effective links, full 3x3.
 template <bool FIELD, int MU>
 __device__ __forceinline__ M3<float> su3c_staple(const Ctx& a, int p, const LexSite& x) {
@@ -193,19 +239,10 @@ __device__ __forceinline__ M3<float> su3c_staple(const Ctx& a, int p, const LexS
   return A;
 }
 
+// Heat-bath or overrelaxation of U_MU(x) given its staple sum A.
 template <bool FIELD, int KIND, int MU>
-__global__ void __maxnreg__(QCD_SU3_PHASE_MAXNREG) su3c_phase_kernel(const Ctx a, int parity) {
-  const int h = blockIdx.x * blockDim.x + threadIdx.x;
-  if (h >= a.g.Vh) return;
-  const Site sc = site_of(a.g, parity, h);
-  LexSite x;
-  x.c[0] = sc.x;
-  x.c[1] = sc.y;
-  x.c[2] = sc.z;
-  x.c[3] = sc.t;
-  x.s = 2 * h + (sc.x & 1);
-  const M3<float> A = su3c_staple<FIELD, MU>(a, parity, x);
-  M3<float> U = su3c_full(su3c_load(a.links, a.g, MU, parity, h));
+__device__ __forceinline__ void su3c_update(const Ctx& a, int parity, int h, const LexSite& x, const M3<float>& A,
+                                            M3<float> U) {
   M3<float> Ut = U;
   if (FIELD && MU == 1) {
     const float2 ph = __ldg(a.phase32 + x.c[0]);
@@ -250,14 +287,42 @@ __global__ void __maxnreg__(QCD_SU3_PHASE_MAXNREG) su3c_phase_kernel(const Ctx a
   SU3Policy<float>::store(a.links, a.g, MU, parity, h, U);
 }
 
+__device__ __forceinline__ LexSite su3c_site(const Ctx& a, int parity, int h) {
+  const Site sc = site_of(a.g, parity, h);
+  LexSite x;
+  x.c[0] = sc.x;
+  x.c[1] = sc.y;
+  x.c[2] = sc.z;
+  x.c[3] = sc.t;
+  x.s = 2 * h + (sc.x & 1);
+  return x;
+}
+
+template <bool FIELD, int KIND, int MU>
+__global__ void __maxnreg__(QCD_SU3_PHASE_MAXNREG) su3c_phase_kernel(const Ctx a, int parity) {
+  const int h = blockIdx.x * blockDim.x + threadIdx.x;
+  if (h >= a.g.Vh) return;
+  const LexSite x = su3c_site(a, parity, h);
+#if QCD_SU3C_PREFETCH
+  su3c_prefetch_all<MU>(a, parity, x);
+#endif
+  const M3<float> A = su3c_staple<FIELD, MU>(a, parity, x);
+  su3c_update<FIELD, KIND, MU>(a, parity, h, x, A, su3c_full(su3c_load(a.links, a.g, MU, parity, h)));
+}
+
+template <bool FIELD, int KIND, int MU>
+inline void su3c_launch_one(const Ctx& a, int parity, int block, cudaStream_t st) {
+  const unsigned grid = grid_for(a.g.Vh, block);
+  su3c_phase_kernel<FIELD, KIND, MU><<<grid, block, 0, st>>>(a, parity);
+}
+
 template <bool FIELD, int KIND>
 inline void su3c_launch_kind(const Ctx& a, int parity, int mu, int block, cudaStream_t st) {
-  const unsigned grid = grid_for(a.g.Vh, block);
   switch (mu) {
-    case 0: su3c_phase_kernel<FIELD, KIND, 0><<<grid, block, 0, st>>>(a, parity); break;
-    case 1: su3c_phase_kernel<FIELD, KIND, 1><<<grid, block, 0, st>>>(a, parity); break;
-    case 2: su3c_phase_kernel<FIELD, KIND, 2><<<grid, block, 0, st>>>(a, parity); break;
-    default: su3c_phase_kernel<FIELD, KIND, 3><<<grid, block, 0, st>>>(a, parity); break;
+    case 0: su3c_launch_one<FIELD, KIND, 0>(a, parity, block, st); break;
+    case 1: su3c_launch_one<FIELD, KIND, 1>(a, parity, block, st); break;
+    case 2: su3c_launch_one<FIELD, KIND, 2>(a, parity, block, st); break;
+    default: su3c_launch_one<FIELD, KIND, 3>(a, parity, block, st); break;
   }
 }
 
