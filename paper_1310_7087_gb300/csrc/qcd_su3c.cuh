@@ -16,11 +16,6 @@
 
 #include "qcd_kernels.cuh"
 
-// Issue L2 prefetches for all gathered links before the staple (more memory
-// requests in flight without holding registers).
-#ifndef QCD_SU3C_PREFETCH
-#define QCD_SU3C_PREFETCH 0
-#endif
 
 
 namespace qcd {
@@ -164,45 +159,6 @@ __device__ __forceinline__ Rows2 su3c_eff(const Ctx& a, int par, const LexSite& 
   return r;
 }
 
-// Ask L2 for the three 16-byte vectors of link (D, par, site) ahead of use.
-template <int D>
-__device__ __forceinline__ void su3c_prefetch(const Ctx& a, int par, const LexSite& x) {
-  const float4* p = reinterpret_cast<const float4*>(a.links);
-#pragma unroll
-  for (int c = 0; c < 3; ++c)
-    asm volatile("prefetch.global.L2 [%0];" ::"l"(p + vidx(a.g, c, D, par, x.s >> 1)));
-}
-
-// All 18 gathered links of U_MU(x) and the link itself.
-template <int MU>
-__device__ __forceinline__ void su3c_prefetch_all(const Ctx& a, int p, const LexSite& x) {
-  const LexSite xp = su3c_step<MU, +1>(a.g, x);
-  su3c_prefetch<MU>(a, p, x);
-#pragma unroll
-  for (int nu = 0; nu < 4; ++nu) {
-    if (nu == MU) continue;
-    switch (nu) {
-#define QCD_SU3C_PF(NU)                                             \
-  case NU: {                                                        \
-    const LexSite xpn = su3c_step<NU, +1>(a.g, x);                  \
-    const LexSite xmn = su3c_step<NU, -1>(a.g, x);                  \
-    su3c_prefetch<NU>(a, p ^ 1, xp);                                \
-    su3c_prefetch<MU>(a, p ^ 1, xpn);                               \
-    su3c_prefetch<NU>(a, p, x);                                     \
-    su3c_prefetch<MU>(a, p ^ 1, xmn);                               \
-    su3c_prefetch<NU>(a, p, su3c_step<NU, -1>(a.g, xp));            \
-    su3c_prefetch<NU>(a, p ^ 1, xmn);                               \
-    break;                                                          \
-  }
-      QCD_SU3C_PF(0)
-      QCD_SU3C_PF(1)
-      QCD_SU3C_PF(2)
-      QCD_SU3C_PF(3)
-#undef QCD_SU3C_PF
-    }
-  }
-}
-
 // Staple sum of U_MU(x) (x of parity p) on effective links, full 3x3.
 template <bool FIELD, int MU>
 __device__ __forceinline__ M3<float> su3c_staple(const Ctx& a, int p, const LexSite& x) {
@@ -303,9 +259,6 @@ __global__ void __maxnreg__(QCD_SU3_PHASE_MAXNREG) su3c_phase_kernel(const Ctx a
   const int h = blockIdx.x * blockDim.x + threadIdx.x;
   if (h >= a.g.Vh) return;
   const LexSite x = su3c_site(a, parity, h);
-#if QCD_SU3C_PREFETCH
-  su3c_prefetch_all<MU>(a, parity, x);
-#endif
   const M3<float> A = su3c_staple<FIELD, MU>(a, parity, x);
   su3c_update<FIELD, KIND, MU>(a, parity, h, x, A, su3c_full(su3c_load(a.links, a.g, MU, parity, h)));
 }
