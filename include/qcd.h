@@ -142,6 +142,22 @@ int qcd_get_exhausted(qcd_lattice *lat, unsigned long long *count);
 int qcd_set_block(qcd_lattice *lat, int threads);
 int qcd_get_block(const qcd_lattice *lat, int *threads);
 
+/* Checkpoint / resume (the paper's portable saved computation state, sec. 3.1
+ * and sec. 6).  The random numbers are counter-based, so the state is the
+ * links plus (seed, sweep counter, NHIT): resuming reproduces the
+ * uninterrupted run bit for bit.  File: 80-byte little-endian header (magic
+ * "QCDGB300", version 1, group, storage, Ns, Nt, flux, NHIT, lattice id, sweep
+ * counter, seed, beta, NHIT-exhaustion count) followed by the links in the
+ * canonical FP64 layout, so a file written with one storage loads into
+ * either.
+ *   qcd_save: writes `path` (overwrites); synchronizes the stream.
+ *   qcd_lattice_load: creates a lattice from `path` with the given storage
+ *   (QCD_FP64_PLAIN or QCD_FP32_COMPRESSED; FP32 rounds FP64 links) on
+ *   `stream`.  QCD_ERR_INVALID_ARG for an unreadable or malformed file. */
+int qcd_save(qcd_lattice *lat, const char *path);
+int qcd_lattice_load(qcd_lattice **out, const char *path, int precision,
+                     void *stream);
+
 /* Live kernel timing (the paper's optional run-time profiling of kernels,
  * sec. 3.2).  When enabled, CUDA events are recorded on the lattice's stream
  * around every kernel the sweep and the measurements launch (inside the

@@ -53,6 +53,8 @@ SIGNATURES = {
     "qcd_get_exhausted": (_i, [_vp, _P(ctypes.c_ulonglong)]),
     "qcd_set_block": (_i, [_vp, _i]),
     "qcd_get_block": (_i, [_vp, _P(_i)]),
+    "qcd_save": (_i, [_vp, ctypes.c_char_p]),
+    "qcd_lattice_load": (_i, [_P(_vp), ctypes.c_char_p, _i, _vp]),
     "qcd_set_profiling": (_i, [_vp, _i]),
     "qcd_get_profile": (_i, [_vp, _P(_d), _P(ctypes.c_ulonglong)]),
     "qcd_measure_noalloc": (_i, [_vp, _i, _i, _i, _i, _i, _P(_d), _P(_d), _vp]),
@@ -213,6 +215,16 @@ def qcd_get_block(h) -> int:
     v = ctypes.c_int()
     _check(lib().qcd_get_block(h, ctypes.byref(v)))
     return v.value
+
+
+def qcd_save(h, path: str) -> None:
+    _check(lib().qcd_save(h, os.fsencode(path)))
+
+
+def qcd_lattice_load(path: str, precision=QCD_FP32_COMPRESSED, stream=None) -> ctypes.c_void_p:
+    h = ctypes.c_void_p()
+    _check(lib().qcd_lattice_load(ctypes.byref(h), os.fsencode(path), precision, _stream_handle(stream)))
+    return h
 
 
 def qcd_set_profiling(h, enable: bool) -> None:
@@ -402,6 +414,24 @@ class Lattice:
     @sweep_counter.setter
     def sweep_counter(self, v):
         qcd_set_sweep(self.h, v)
+
+    def save(self, path):
+        qcd_save(self.h, path)
+
+    @classmethod
+    def load(cls, path, precision=QCD_FP32_COMPRESSED, stream=None):
+        """A lattice restored from a checkpoint written by ``save``."""
+        import struct
+        with open(path, "rb") as f:
+            head = f.read(72)
+        group, _, Ns, Nt, flux = struct.unpack_from("<IIIIi", head, 12)
+        seed, beta = struct.unpack_from("<Qd", head, 48)
+        self = cls.__new__(cls)
+        self.group, self.Ns, self.Nt = group, Ns, Nt
+        self.V = Ns ** 3 * Nt
+        self.beta, self.flux, self.precision, self.seed = beta, flux, precision, seed
+        self.h = qcd_lattice_load(path, precision, stream)
+        return self
 
     @property
     def exhausted(self):

@@ -643,6 +643,95 @@ int qcd_get_profile(qcd_lattice* L, double* ms, unsigned long long* launches) {
   return QCD_OK;
 }
 
+namespace {
+struct CheckpointHeader {
+  char magic[8];
+  uint32_t version, group, precision, Ns, Nt;
+  int32_t flux;
+  uint32_t nhit, lattice_id, sweep, pad;
+  uint64_t seed;
+  double beta;
+  uint64_t exhausted;
+};
+static_assert(sizeof(CheckpointHeader) == 72, "checkpoint header layout");
+constexpr char kMagic[8] = {'Q', 'C', 'D', 'G', 'B', '3', '0', '0'};
+}  // namespace
+
+int qcd_save(qcd_lattice* L, const char* path) {
+  if (int rc = check(L)) return rc;
+  if (!path) return set_error(QCD_ERR_INVALID_ARG, "path is null");
+  CheckpointHeader h{};
+  std::memcpy(h.magic, kMagic, 8);
+  h.version = 1;
+  h.group = uint32_t(L->group);
+  h.precision = uint32_t(L->precision);
+  h.Ns = uint32_t(L->Ns);
+  h.Nt = uint32_t(L->Nt);
+  h.flux = L->flux;
+  h.nhit = uint32_t(L->nhit);
+  h.lattice_id = L->lattice_id;
+  h.seed = L->seed;
+  h.beta = L->beta;
+  if (int rc = qcd_get_sweep(L, &h.sweep)) return rc;
+  unsigned long long ex = 0;
+  if (int rc = qcd_get_exhausted(L, &ex)) return rc;
+  h.exhausted = ex;
+  const size_t n = canonical_bytes(L) / sizeof(double);
+  std::vector<double> buf(n);
+  if (int rc = qcd_get_links(L, buf.data())) return rc;
+  FILE* f = fopen(path, "wb");
+  if (!f) return set_error(QCD_ERR_INVALID_ARG, "cannot open %s for writing", path);
+  const uint64_t pad8 = 0;
+  const bool ok = fwrite(&h, sizeof h, 1, f) == 1 && fwrite(&pad8, 8, 1, f) == 1 &&
+                  fwrite(buf.data(), sizeof(double), n, f) == n;
+  if (fclose(f) != 0 || !ok) return set_error(QCD_ERR_INVALID_ARG, "writing %s failed", path);
+  return QCD_OK;
+}
+
+int qcd_lattice_load(qcd_lattice** out, const char* path, int precision, void* stream) {
+  if (!out || !path) return set_error(QCD_ERR_INVALID_ARG, "null argument");
+  *out = nullptr;
+  FILE* f = fopen(path, "rb");
+  if (!f) return set_error(QCD_ERR_INVALID_ARG, "cannot open %s", path);
+  CheckpointHeader h{};
+  uint64_t pad8 = 0;
+  if (fread(&h, sizeof h, 1, f) != 1 || fread(&pad8, 8, 1, f) != 1 || std::memcmp(h.magic, kMagic, 8) != 0 ||
+      h.version != 1 || (h.group != 2 && h.group != 3) || h.Ns < 2 || h.Nt < 2 || h.Ns > 1290 || h.Nt > (1u << 30)) {
+    fclose(f);
+    return set_error(QCD_ERR_INVALID_ARG, "%s is not a version-1 checkpoint", path);
+  }
+  qcd_lattice* L = nullptr;
+  int rc = qcd_lattice_create(&L, int(h.group), int(h.Ns), int(h.Nt), h.beta, h.flux, precision, QCD_COLD, h.seed,
+                              stream);
+  if (rc) {
+    fclose(f);
+    return rc;
+  }
+  const size_t n = canonical_bytes(L) / sizeof(double);
+  std::vector<double> buf(n);
+  const bool ok = fread(buf.data(), sizeof(double), n, f) == n;
+  fclose(f);
+  if (!ok) {
+    qcd_lattice_destroy(L);
+    return set_error(QCD_ERR_INVALID_ARG, "%s is truncated", path);
+  }
+  L->nhit = int(h.nhit);
+  L->lattice_id = h.lattice_id;
+  if ((rc = qcd_set_links(L, buf.data())) || (rc = qcd_set_sweep(L, h.sweep))) {
+    qcd_lattice_destroy(L);
+    return rc;
+  }
+  const unsigned long long ex = h.exhausted;
+  cudaError_t e = cudaMemcpyAsync(L->d_exhausted, &ex, sizeof ex, cudaMemcpyHostToDevice, L->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(L->stream);
+  if (e != cudaSuccess) {
+    qcd_lattice_destroy(L);
+    return set_error(QCD_ERR_CUDA, "load: %s", cudaGetErrorString(e));
+  }
+  *out = L;
+  return QCD_OK;
+}
+
 int qcd_get_exhausted(qcd_lattice* L, unsigned long long* count) {
   if (int rc = check(L)) return rc;
   if (!count) return set_error(QCD_ERR_INVALID_ARG, "count is null");
