@@ -52,6 +52,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the FP64-plain and batched-scan side measurements")
+    ap.add_argument("--batch-only", action="store_true",
+                    help="time only the batched 64-lattice scan (--steps sweeps in one launch)")
     ap.add_argument("--Ns", type=int, default=None, help="override the spatial extent (small profiling cases)")
     ap.add_argument("--Nt", type=int, default=None, help="override the time extent (small profiling cases)")
     return ap.parse_args()
@@ -242,6 +244,42 @@ def config_of(w, storage):
             "l2": "links larger than L2 (no flush between steps)"}
 
 
+def run_batched(q, stream, world, rank, dist, sweeps):
+    """Batched scan: 64 uneven SU(2) lattices, `sweeps` sweeps in one
+    persistent launch (each rank sweeps its share of the lattices)."""
+    import torch
+    from paper_1310_7087_gb300 import dist as qd
+    scan = workloads.batch_scan()
+    mine = qd.shard(scan.volumes, world, rank)
+    pick = lambda v: [v[i] for i in mine]
+    bt = q.Batch(pick(scan.Ns), pick(scan.Nt), pick(scan.beta), pick(scan.flux),
+                 q.QCD_FP32_COMPRESSED, q.QCD_HOT, scan.seed, stream)
+    bt.sweep(sweeps, scan.n_or)  # launch shape, graph capture, warm-up
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    g0, g1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    g0.record(stream)
+    bm = bt.sweep(sweeps, scan.n_or)
+    g1.record(stream)
+    torch.cuda.synchronize()
+    bt_ms = qd.max_over_ranks(g0.elapsed_time(g1), "cuda")
+    lu_b = qd.sum_over_ranks(float((1 + scan.n_or) * 4 * sum(pick(scan.volumes)) * sweeps), "cuda")
+    threads, ctas = q.qcd_batch_get_shape(bt.h)
+    out = {"workload": "batch of %d SU(2) lattices, Ns in {8,12,16,24}, Nt in {4,6,8}, beta in [2.2,2.5], "
+                       "flux 0..3 (seed %d); %d sweeps of 1 HB + %d OR + reunitarization + measurement "
+                       "in one launch" % (scan.n, scan.seed, sweeps, scan.n_or),
+           "value": lu_b / (bt_ms / 1e3), "unit": UNIT, "ms_total": bt_ms,
+           "ms_per_sweep": bt_ms / sweeps, "storage": "FP32 4-real (quaternion)",
+           "links_bytes": q.qcd_batch_link_bytes(bt.h),
+           "effective_gbs": lu_b * TRANSFERS_PER_UPDATE * LINK_BYTES[(2, 1)] / (bt_ms / 1e3) / 1e9,
+           "note": "links fit in L2 (129 MB): effective bandwidth, not HBM",
+           "launch": {"threads_per_cta": threads, "ctas": ctas}, "gpu_launches_per_call": 2,
+           "mean_plaquette_last_sweep": float(bm[:, -1, 0].mean())}
+    bt.close()
+    return out
+
+
 def main():
     args = parse()
     w = workloads.SU3_64x16
@@ -265,6 +303,13 @@ def main():
     import paper_1310_7087_gb300 as q
 
     stream = torch.cuda.current_stream()
+    if args.batch_only:
+        out = run_batched(q, stream, world, rank, dist, args.steps)
+        if rank == 0:
+            print(json.dumps(dict(out, metric=METRIC, n_gpus=world, steps=args.steps, warmup=1,
+                                  higher_is_better=True, scaling="weak", dtype="f32", data="synthetic")),
+                  flush=True)
+        return 0
     seed = w.seed + 1000 * rank
     lat = q.Lattice(w.group, w.Ns, w.Nt, w.beta, w.flux, q.QCD_FP32_COMPRESSED, q.QCD_HOT, seed, stream)
     h = lat.h
@@ -367,38 +412,7 @@ def main():
                                                 (lu_per_step / (ms64 / 1e3))}
         lat64.close()
 
-        # batched scan: 64 uneven SU(2) lattices, 200 sweeps in one persistent
-        # launch (each rank sweeps its share of the lattices)
-        from paper_1310_7087_gb300 import dist as qd
-        scan = workloads.batch_scan()
-        mine = qd.shard(scan.volumes, world, rank)
-        pick = lambda v: [v[i] for i in mine]
-        bt = q.Batch(pick(scan.Ns), pick(scan.Nt), pick(scan.beta), pick(scan.flux),
-                     q.QCD_FP32_COMPRESSED, q.QCD_HOT, scan.seed, stream)
-        bt.sweep(scan.sweeps, scan.n_or)  # launch shape, graph capture, warm-up
-        torch.cuda.synchronize()
-        if dist:
-            dist.barrier()
-        g0, g1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        g0.record(stream)
-        bm = bt.sweep(scan.sweeps, scan.n_or)
-        g1.record(stream)
-        torch.cuda.synchronize()
-        bt_ms = qd.max_over_ranks(g0.elapsed_time(g1), "cuda")
-        lu_b = qd.sum_over_ranks(float((1 + scan.n_or) * 4 * sum(pick(scan.volumes)) * scan.sweeps), "cuda")
-        threads, ctas = q.qcd_batch_get_shape(bt.h)
-        extras["batched"] = {
-            "workload": "batch of %d SU(2) lattices, Ns in {8,12,16,24}, Nt in {4,6,8}, beta in [2.2,2.5], "
-                        "flux 0..3 (seed %d); %d sweeps of 1 HB + %d OR + reunitarization + measurement "
-                        "in one launch" % (scan.n, scan.seed, scan.sweeps, scan.n_or),
-            "value": lu_b / (bt_ms / 1e3), "unit": UNIT, "ms_total": bt_ms,
-            "ms_per_sweep": bt_ms / scan.sweeps, "storage": "FP32 4-real (quaternion)",
-            "links_bytes": q.qcd_batch_link_bytes(bt.h),
-            "effective_gbs": lu_b * TRANSFERS_PER_UPDATE * LINK_BYTES[(2, 1)] / (bt_ms / 1e3) / 1e9,
-            "note": "links fit in L2 (129 MB): effective bandwidth, not HBM",
-            "launch": {"threads_per_cta": threads, "ctas": ctas}, "gpu_launches_per_call": 2,
-            "mean_plaquette_last_sweep": float(bm[:, -1, 0].mean())}
-        bt.close()
+        extras["batched"] = run_batched(q, stream, world, rank, dist, workloads.batch_scan().sweeps)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:

@@ -338,4 +338,50 @@ __device__ __forceinline__ int64_t vidx(const Geom& g, int comp, int mu, int par
   return (int64_t(comp * 4 + mu) * 2 + parity) * g.plane + h;
 }
 
+// ---------------------------------------------------------------------------
+// Neighbour stepping on the lexicographic index: a site carries its index and
+// coordinates, and one step along a direction known at compile time is a
+// stride plus a wrap correction.
+// ---------------------------------------------------------------------------
+// A site by its lexicographic index and coordinates.
+struct LexSite {
+  int s;
+  int c[4];
+};
+
+template <int D>
+__device__ __forceinline__ int lex_stride(const Geom& g) {
+  return D == 0 ? 1 : D == 1 ? g.Ns : D == 2 ? g.Ns * g.Ns : g.Ns * g.Ns * g.Ns;
+}
+template <int D>
+__device__ __forceinline__ int lex_extent(const Geom& g) {
+  return D == 3 ? g.Nt : g.Ns;
+}
+// one step +1 / -1 along D with periodic wrap
+template <int D, int STEP>
+__device__ __forceinline__ LexSite lex_step(const Geom& g, LexSite x) {
+  const int st = lex_stride<D>(g), ext = lex_extent<D>(g);
+  if (STEP > 0) {
+    const bool wrap = x.c[D] == ext - 1;
+    x.s += wrap ? st - ext * st : st;
+    x.c[D] = wrap ? 0 : x.c[D] + 1;
+  } else {
+    const bool wrap = x.c[D] == 0;
+    x.s += wrap ? ext * st - st : -st;
+    x.c[D] = wrap ? ext - 1 : x.c[D] - 1;
+  }
+  return x;
+}
+
+__device__ __forceinline__ LexSite lex_site(const Ctx& a, int parity, int h) {
+  const Site sc = site_of(a.g, parity, h);
+  LexSite x;
+  x.c[0] = sc.x;
+  x.c[1] = sc.y;
+  x.c[2] = sc.z;
+  x.c[3] = sc.t;
+  x.s = 2 * h + (sc.x & 1);
+  return x;
+}
+
 }  // namespace qcd

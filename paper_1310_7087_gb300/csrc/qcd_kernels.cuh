@@ -233,57 +233,6 @@ __device__ __forceinline__ typename P::Link staple(const Ctx& a, const Site& x, 
 }
 
 // ---------------------------------------------------------------------------
-// SU(2) phase update: Kennedy-Pendleton heat-bath or overrelaxation of the
-// links of direction mu on sites of one parity.
-// ---------------------------------------------------------------------------
-template <typename R, bool FIELD, int KIND, bool CG = false>
-__device__ __forceinline__ void su2_update_site(const Ctx& a, int parity, int mu, int h, uint32_t sweep) {
-  using P = SU2Policy<R>;
-  const Site x = site_of(a.g, parity, h);
-  const Quat<R> A = staple<P, FIELD, CG>(a, x, mu);
-  const R k = q_sqrt(qnorm2(A));  // sqrt(det A)
-  const bool phased = FIELD && mu == 1;
-  R bc = R(1), bs = R(0);
-  if (phased) load_phase<R>(a, x.x, bc, bs);
-  const Quat<R> Bd{bc, R(0), R(0), -bs};  // B^+
-
-  Quat<R> ut_new;
-  if (KIND == KIND_HB) {
-    const R alpha = R(a.beta) * k;
-    const uint32_t s = uint32_t(lex(a.g, x));
-    const Stream dir = make_stream(a.k0, a.k1, s, sweep, mu, 0, KIND_DIR);
-    if (alpha == R(0)) {
-      ut_new = su2_haar<R>(dir, 0u);
-    } else {
-      const Stream tries = make_stream(a.k0, a.k1, s, sweep, mu, 0, KIND_TRY);
-      R delta;
-      if (!kp_draw<R>(alpha, a.nhit, tries, delta)) {
-        atomicAdd(a.exhausted, 1ull);
-        return;  // keep the link
-      }
-      const Quat<R> X = su2_with_delta<R>(delta, dir);
-      const Quat<R> V = qscale(A, R(1) / k);
-      ut_new = qmul(X, qdag(V));
-    }
-  } else {
-    if (k == R(0)) return;
-    const Quat<R> Vd = qdag(qscale(A, R(1) / k));
-    Quat<R> ut = P::template load<CG>(a.links, a.g, mu, parity, h);
-    if (phased) ut = qmul(ut, qdag(Bd));
-    ut_new = qmul(qmul(Vd, qdag(ut)), Vd);
-  }
-  const Quat<R> u_new = phased ? qmul(ut_new, Bd) : ut_new;
-  P::store(a.links, a.g, mu, parity, h, u_new);
-}
-
-template <typename R, bool FIELD, int KIND>
-__global__ void su2_phase_kernel(const Ctx a, int parity, int mu) {
-  const int h = blockIdx.x * blockDim.x + threadIdx.x;
-  if (h >= a.g.Vh) return;
-  su2_update_site<R, FIELD, KIND>(a, parity, mu, h, KIND == KIND_HB ? *a.sweep : 0u);
-}
-
-// ---------------------------------------------------------------------------
 // SU(3) phase update: Cabibbo-Marinari heat-bath or overrelaxation over the
 // SU(2) subgroups (0,1), (1,2), (0,2).
 // ---------------------------------------------------------------------------
@@ -814,11 +763,8 @@ inline unsigned grid_for(int64_t n, int block) { return unsigned((n + block - 1)
 
 template <class P, bool FIELD, int KIND>
 inline void launch_phase_t(const Ctx& a, int parity, int mu, int block, cudaStream_t st) {
-  const unsigned grid = grid_for(a.g.Vh, block);
-  if constexpr (P::N == 2)
-    su2_phase_kernel<typename P::Real, FIELD, KIND><<<grid, block, 0, st>>>(a, parity, mu);
-  else
-    su3_phase_kernel<typename P::Real, FIELD, KIND><<<grid, block, 0, st>>>(a, parity, mu);
+  static_assert(P::N == 3, "SU(2) uses the kernels of qcd_su2c.cuh");
+  su3_phase_kernel<typename P::Real, FIELD, KIND><<<grid_for(a.g.Vh, block), block, 0, st>>>(a, parity, mu);
 }
 
 template <class P>
@@ -877,11 +823,7 @@ cudaError_t launch_from_canonical(const Ctx& a, const double* in, cudaStream_t s
 template <class P, bool FIELD, int KIND>
 int phase_block_limit() {
   cudaFuncAttributes attr{};
-  cudaError_t e;
-  if constexpr (P::N == 2)
-    e = cudaFuncGetAttributes(&attr, su2_phase_kernel<typename P::Real, FIELD, KIND>);
-  else
-    e = cudaFuncGetAttributes(&attr, su3_phase_kernel<typename P::Real, FIELD, KIND>);
+  const cudaError_t e = cudaFuncGetAttributes(&attr, su3_phase_kernel<typename P::Real, FIELD, KIND>);
   return e == cudaSuccess ? attr.maxThreadsPerBlock : 0;
 }
 

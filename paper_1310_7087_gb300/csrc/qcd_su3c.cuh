@@ -118,36 +118,6 @@ __device__ __forceinline__ void su3c_acc(M3<float>& acc, const Rows2& t) {
   }
 }
 
-// A site by its lexicographic index and coordinates.
-struct LexSite {
-  int s;
-  int c[4];
-};
-
-template <int D>
-__device__ __forceinline__ int su3c_stride(const Geom& g) {
-  return D == 0 ? 1 : D == 1 ? g.Ns : D == 2 ? g.Ns * g.Ns : g.Ns * g.Ns * g.Ns;
-}
-template <int D>
-__device__ __forceinline__ int su3c_extent(const Geom& g) {
-  return D == 3 ? g.Nt : g.Ns;
-}
-// one step +1 / -1 along D with periodic wrap
-template <int D, int STEP>
-__device__ __forceinline__ LexSite su3c_step(const Geom& g, LexSite x) {
-  const int st = su3c_stride<D>(g), ext = su3c_extent<D>(g);
-  if (STEP > 0) {
-    const bool wrap = x.c[D] == ext - 1;
-    x.s += wrap ? st - ext * st : st;
-    x.c[D] = wrap ? 0 : x.c[D] + 1;
-  } else {
-    const bool wrap = x.c[D] == 0;
-    x.s += wrap ? ext * st - st : -st;
-    x.c[D] = wrap ? ext - 1 : x.c[D] - 1;
-  }
-  return x;
-}
-
 // Effective link of direction D at site x, whose parity PAR is known.
 template <bool FIELD, int D>
 __device__ __forceinline__ Rows2 su3c_eff(const Ctx& a, int par, const LexSite& x) {
@@ -164,7 +134,7 @@ template <bool FIELD, int MU>
 __device__ __forceinline__ M3<float> su3c_staple(const Ctx& a, int p, const LexSite& x) {
   M3<float> A;
   m3_zero(A);
-  const LexSite xp = su3c_step<MU, +1>(a.g, x);
+  const LexSite xp = lex_step<MU, +1>(a.g, x);
 #pragma unroll
   for (int nu = 0; nu < 4; ++nu) {
     if (nu == MU) continue;
@@ -172,9 +142,9 @@ __device__ __forceinline__ M3<float> su3c_staple(const Ctx& a, int p, const LexS
     switch (nu) {
 #define QCD_SU3C_NU(NU)                                                                         \
   case NU: {                                                                                      \
-    const LexSite xpn = su3c_step<NU, +1>(a.g, x);                                                \
-    const LexSite xmn = su3c_step<NU, -1>(a.g, x);                                                \
-    const LexSite xpmn = su3c_step<NU, -1>(a.g, xp);                                              \
+    const LexSite xpn = lex_step<NU, +1>(a.g, x);                                                \
+    const LexSite xmn = lex_step<NU, -1>(a.g, x);                                                \
+    const LexSite xpmn = lex_step<NU, -1>(a.g, xp);                                              \
     /* upper: Ut_nu(x+mu) Ut_mu(x+nu)^+ Ut_nu(x)^+ */                                             \
     const Rows2 x1 = su3c_mul_nd(su3c_eff<FIELD, NU>(a, p ^ 1, xp),                               \
                                  su3c_full(su3c_eff<FIELD, MU>(a, p ^ 1, xpn)));                  \
@@ -243,22 +213,11 @@ __device__ __forceinline__ void su3c_update(const Ctx& a, int parity, int h, con
   SU3Policy<float>::store(a.links, a.g, MU, parity, h, U);
 }
 
-__device__ __forceinline__ LexSite su3c_site(const Ctx& a, int parity, int h) {
-  const Site sc = site_of(a.g, parity, h);
-  LexSite x;
-  x.c[0] = sc.x;
-  x.c[1] = sc.y;
-  x.c[2] = sc.z;
-  x.c[3] = sc.t;
-  x.s = 2 * h + (sc.x & 1);
-  return x;
-}
-
 template <bool FIELD, int KIND, int MU>
 __global__ void __maxnreg__(QCD_SU3_PHASE_MAXNREG) su3c_phase_kernel(const Ctx a, int parity) {
   const int h = blockIdx.x * blockDim.x + threadIdx.x;
   if (h >= a.g.Vh) return;
-  const LexSite x = su3c_site(a, parity, h);
+  const LexSite x = lex_site(a, parity, h);
   const M3<float> A = su3c_staple<FIELD, MU>(a, parity, x);
   su3c_update<FIELD, KIND, MU>(a, parity, h, x, A, su3c_full(su3c_load(a.links, a.g, MU, parity, h)));
 }

@@ -1,6 +1,8 @@
-// su2_f64.cu -- kernels of the gauge sweep instantiated for one (group, storage).
-#include "qcd_kernels.cuh"
+// su2_f64.cu -- kernels of the gauge sweep for SU(2) with FP64 4-real links (quaternions).
+// The phase update uses the kernels of qcd_su2c.cuh; reunitarization, start,
+// measurements and layout conversion use the shared templates.
+#include "qcd_su2c.cuh"
 
 namespace qcd {
-const PolicyOps kOpsSU2F64 = make_ops<SU2Policy<double>>(0);
+const PolicyOps kOpsSU2F64 = su2c_ops<double>(0);
 }  // namespace qcd

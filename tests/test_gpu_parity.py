@@ -92,11 +92,15 @@ WHOLE_SWEEP = [c for c in CASES if c[1] == FP64_PLAIN or c[0] == 2]
 
 @pytest.mark.parametrize("case", WHOLE_SWEEP, ids=[IDS[CASES.index(c)] for c in WHOLE_SWEEP])
 def test_one_sweep_from_shared_start(q, case):
-    """FP64 storage (both groups) and FP32 SU(2): one whole graph-launched
-    sweep, HB + 4 OR (SU(3)) or HB + 1 OR (SU(2)), from a shared start."""
+    """One whole graph-launched sweep from a shared start: HB + 4 OR (SU(3))
+    or HB + 1 OR (SU(2)) with FP64 storage; an SU(2) heat-bath pass with FP32
+    storage.  The chain amplifies FP32 rounding past 1e-5 within an OR pass
+    (and, for SU(3), through small subgroup norms within a heat-bath pass), so
+    FP32 SU(3) and every FP32 OR kernel are held to the bar kernel by kernel
+    (test_sweep_schedule_kernel_by_kernel)."""
     lat, orc = pair(q, case)
     orc.set_links(lat.get_links())
-    n_or = 4 if case[0] == 3 else 1
+    n_or = (4 if case[0] == 3 else 1) if case[1] == FP64_PLAIN else 0
     lat.sweep(1, n_or, 7)
     orc.sweep(1, n_or, 7)
     check_links(lat.get_links(), orc.get_links(), case[1], "sweep")
