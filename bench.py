@@ -75,13 +75,16 @@ def load_peaks():
     return 6800.0, "fallback"
 
 
+# Source files that define the SU(3) FP32 phase kernels (the dominant kernel).
+PHASE_KERNEL_SOURCES = ("qcd_device.cuh", "qcd_internal.h", "qcd_kernels.cuh", "qcd_su3c.cuh", "su3_f32.cu")
+
+
 def kernel_source_sha():
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_1310_7087_gb300", "csrc")
-    for name in sorted(os.listdir(csrc)):
-        if name.endswith((".cu", ".cuh", ".h")):
-            with open(os.path.join(csrc, name), "rb") as f:
-                h.update(name.encode() + f.read())
+    for name in PHASE_KERNEL_SOURCES:
+        with open(os.path.join(csrc, name), "rb") as f:
+            h.update(name.encode() + f.read())
     return h.hexdigest()[:16]
 
 

@@ -384,4 +384,23 @@ __device__ __forceinline__ LexSite lex_site(const Ctx& a, int parity, int h) {
   return x;
 }
 
+// Site of one parity for thread index i, enumerated x (in pairs) fastest, then
+// y, then t, then z.  Each phase still visits every site once, but successive
+// CTAs step through t before z, so the t-neighbour of a site is gathered a
+// few CTAs after it was last read (not a whole Ns^3 volume later) and is still
+// in L2: the longest reuse distance drops from Ns^3/2 to Ns^2 Nt/2 sites.
+__device__ __forceinline__ LexSite lex_site_ytz(const Geom& g, int parity, int i) {
+  int r = 2 * i;
+  LexSite x;
+  const int x0 = r % g.Ns;
+  r /= g.Ns;
+  x.c[1] = r % g.Ns;
+  r /= g.Ns;
+  x.c[3] = r % g.Nt;
+  x.c[2] = r / g.Nt;
+  x.c[0] = x0 + ((parity + x.c[1] + x.c[2] + x.c[3]) & 1);
+  x.s = x.c[0] + g.Ns * (x.c[1] + g.Ns * (x.c[2] + g.Ns * x.c[3]));
+  return x;
+}
+
 }  // namespace qcd

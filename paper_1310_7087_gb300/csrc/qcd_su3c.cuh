@@ -215,9 +215,10 @@ __device__ __forceinline__ void su3c_update(const Ctx& a, int parity, int h, con
 
 template <bool FIELD, int KIND, int MU>
 __global__ void __maxnreg__(QCD_SU3_PHASE_MAXNREG) su3c_phase_kernel(const Ctx a, int parity) {
-  const int h = blockIdx.x * blockDim.x + threadIdx.x;
-  if (h >= a.g.Vh) return;
-  const LexSite x = lex_site(a, parity, h);
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= a.g.Vh) return;
+  const LexSite x = lex_site_ytz(a.g, parity, i);
+  const int h = x.s >> 1;
   const M3<float> A = su3c_staple<FIELD, MU>(a, parity, x);
   su3c_update<FIELD, KIND, MU>(a, parity, h, x, A, su3c_full(su3c_load(a.links, a.g, MU, parity, h)));
 }
