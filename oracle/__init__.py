@@ -22,6 +22,8 @@ _LIB = os.path.join(_HERE, "liboracle.so")
 
 HEATBATH = 0
 OVERRELAX = 1
+FIELD_LINKS = 0   # background as a phase on the dynamical y-links
+FIELD_FROZEN = 1  # background on the frozen spatial links of the t = 0 slice
 
 # -ffp-contract=off: no fused multiply-add, so the oracle rounds the same way
 # on x86-64 and aarch64 hosts.
@@ -58,6 +60,8 @@ def lib() -> ctypes.CDLL:
         L.oracle_uniform.restype = d
         L.oracle_create.argtypes = [i, i, i, d, i, i, u32]
         L.oracle_create.restype = vp
+        L.oracle_create_ex.argtypes = [i, i, i, d, i, i, u32, i]
+        L.oracle_create_ex.restype = vp
         L.oracle_destroy.argtypes = [vp]
         L.oracle_set_threads.argtypes = [i]
         L.oracle_get_threads.argtypes = []
@@ -139,11 +143,11 @@ class OracleLattice:
     ``[t][z][y][x][mu][row][col]`` (x fastest), complex128."""
 
     def __init__(self, N: int, Ns: int, Nt: int, beta: float, flux: int = 0,
-                 nhit: int = 10, lattice_id: int = 0):
+                 nhit: int = 10, lattice_id: int = 0, field_mode: int = FIELD_LINKS):
         self.N, self.Ns, self.Nt = N, Ns, Nt
         self.V = Ns ** 3 * Nt
-        self.beta, self.flux, self.nhit = beta, flux, nhit
-        h = lib().oracle_create(N, Ns, Nt, beta, flux, nhit, lattice_id)
+        self.beta, self.flux, self.nhit, self.field_mode = beta, flux, nhit, field_mode
+        h = lib().oracle_create_ex(N, Ns, Nt, beta, flux, nhit, lattice_id, field_mode)
         if not h:
             raise ValueError("oracle_create rejected the arguments")
         self._h = h

@@ -37,7 +37,12 @@
  *      link (SU(2)) or is the subgroup rotation (SU(3));
  *   R5 external field: U(1) phase along lambda3 (sigma3 for SU(2)) on y-links,
  *      phi(x) = 2 pi n x / Ns^2, applied on the right, Ut = U B; updates act on
- *      Ut and store U = Ut_new B^dagger;
+ *      Ut and store U = Ut_new B^dagger (effective-link mode; a change of
+ *      variables, so effective-link observables do not depend on n);
+ *   R9 frozen-boundary mode (the field imposed through fixed links, as in the
+ *      background-field studies the paper cites): the spatial links of the
+ *      time slice t = 0 hold B and are never updated or reunitarized, the
+ *      other links carry no phase;
  *   R6 Polyakov loop: (1/N) Tr of the product t = 0 .. Nt-1, averaged over the
  *      Ns^3 spatial sites;
  *   R7 reunitarization after each heat-bath pass's overrelaxation block;
@@ -77,6 +82,7 @@ struct oracle_lattice {
     long V;
     double beta;
     int flux;
+    int field_mode;     /* ORACLE_FIELD_LINKS or ORACLE_FIELD_FROZEN */
     int nhit;
     uint32_t lattice_id;
     uint32_t sweep;     /* heat-bath passes since the start */
@@ -315,11 +321,40 @@ static mat background(const oracle_lattice *L, long s, int mu)
     return b;
 }
 
-/* Effective link Ut = U B. */
+/* The phase the dynamical link carries: B in the effective-link mode, unity
+ * when the field lives on the frozen boundary links. */
+static mat link_phase(const oracle_lattice *L, long s, int mu)
+{
+    if (L->field_mode == ORACLE_FIELD_FROZEN) return mat_identity(L->N);
+    return background(L, s, mu);
+}
+
+/* Effective link Ut = U B (effective-link mode) or U (frozen mode). */
 static mat eff_link(const oracle_lattice *L, long s, int mu)
 {
-    mat u = get_link(L, s, mu), b = background(L, s, mu);
+    mat u = get_link(L, s, mu), b = link_phase(L, s, mu);
     return mat_mul(L->N, &u, &b);
+}
+
+/* Frozen-boundary mode: the spatial links of the time slice t = 0 hold the
+ * background field B and are never updated. */
+static int is_frozen(const oracle_lattice *L, long s, int mu)
+{
+    if (L->field_mode != ORACLE_FIELD_FROZEN || mu == 3) return 0;
+    int c[4];
+    site_coords(L, s, c);
+    return c[3] == 0;
+}
+
+static void set_frozen_links(oracle_lattice *L)
+{
+    if (L->field_mode != ORACLE_FIELD_FROZEN) return;
+    long V3 = (long)L->Ns * L->Ns * L->Ns;
+    for (long s = 0; s < V3; ++s)
+        for (int mu = 0; mu < 3; ++mu) {
+            mat b = background(L, s, mu);
+            put_link(L, s, mu, &b);
+        }
 }
 
 /* Staple sum of U_mu(x) on effective links:
@@ -456,7 +491,7 @@ static int heatbath_su2(const oracle_lattice *L, uint64_t seed, long s, int mu,
     double k = sqrt(det > 0.0 ? det : 0.0);
     double alpha = L->beta * k;
     stream dir = lattice_stream(L, seed, L->sweep, s, mu, 0, KIND_DIR);
-    mat b = background(L, s, mu), bd = mat_dag(2, &b);
+    mat b = link_phase(L, s, mu), bd = mat_dag(2, &b);
     double x[4];
     mat ut_new;
     if (alpha == 0.0) {
@@ -497,7 +532,7 @@ static void overrelax_su2(const oracle_lattice *L, long s, int mu, mat *out)
     mat vd = mat_dag(2, &v);
     mat ut = eff_link(L, s, mu), utd = mat_dag(2, &ut);
     mat ut_new = mat_mul3(2, &vd, &utd, &vd);
-    mat b = background(L, s, mu), bd = mat_dag(2, &b);
+    mat b = link_phase(L, s, mu), bd = mat_dag(2, &b);
     *out = mat_mul(2, &ut_new, &bd);
 }
 
@@ -512,7 +547,7 @@ static int heatbath_su3(const oracle_lattice *L, uint64_t seed, long s, int mu,
                         mat *out)
 {
     mat a = staple(L, s, mu);
-    mat b = background(L, s, mu);
+    mat b = link_phase(L, s, mu);
     mat u = get_link(L, s, mu);
     int exhausted = 0;
     for (int sub = 0; sub < 3; ++sub) {
@@ -553,7 +588,7 @@ static int heatbath_su3(const oracle_lattice *L, uint64_t seed, long s, int mu,
 static void overrelax_su3(const oracle_lattice *L, long s, int mu, mat *out)
 {
     mat a = staple(L, s, mu);
-    mat b = background(L, s, mu);
+    mat b = link_phase(L, s, mu);
     mat u = get_link(L, s, mu);
     for (int sub = 0; sub < 3; ++sub) {
         int i = SUBGROUP[sub][0], j = SUBGROUP[sub][1];
@@ -575,6 +610,10 @@ static void overrelax_su3(const oracle_lattice *L, long s, int mu, mat *out)
 static int update_link(const oracle_lattice *L, int kind, uint64_t seed, long s,
                        int mu, mat *out)
 {
+    if (is_frozen(L, s, mu)) {
+        *out = get_link(L, s, mu);
+        return 0;
+    }
     if (kind == ORACLE_HEATBATH)
         return L->N == 2 ? heatbath_su2(L, seed, s, mu, out)
                          : heatbath_su3(L, seed, s, mu, out);
@@ -621,14 +660,22 @@ static mat reunitarize_one(int N, const mat *m)
 oracle_lattice *oracle_create(int N, int Ns, int Nt, double beta, int flux,
                               int nhit, uint32_t lattice_id)
 {
+    return oracle_create_ex(N, Ns, Nt, beta, flux, nhit, lattice_id,
+                            ORACLE_FIELD_LINKS);
+}
+
+oracle_lattice *oracle_create_ex(int N, int Ns, int Nt, double beta, int flux,
+                                 int nhit, uint32_t lattice_id, int field_mode)
+{
     if ((N != 2 && N != 3) || Ns < 2 || Nt < 2 || (Ns & 1) || (Nt & 1) ||
-        beta < 0.0 || nhit < 1)
+        beta < 0.0 || nhit < 1 ||
+        (field_mode != ORACLE_FIELD_LINKS && field_mode != ORACLE_FIELD_FROZEN))
         return NULL;
     oracle_lattice *L = calloc(1, sizeof *L);
     if (!L) return NULL;
     L->N = N; L->Ns = Ns; L->Nt = Nt;
     L->V = (long)Ns * Ns * Ns * Nt;
-    L->beta = beta; L->flux = flux; L->nhit = nhit;
+    L->beta = beta; L->flux = flux; L->nhit = nhit; L->field_mode = field_mode;
     L->lattice_id = lattice_id;
     L->U = calloc((size_t)L->V * 4 * N * N, sizeof(cplx));
     if (!L->U) {
@@ -669,6 +716,7 @@ void oracle_cold_start(oracle_lattice *L)
     mat one = mat_identity(L->N);
     for (long s = 0; s < L->V; ++s)
         for (int mu = 0; mu < 4; ++mu) put_link(L, s, mu, &one);
+    set_frozen_links(L);
     L->sweep = 0;
     L->exhausted = 0;
 }
@@ -691,6 +739,7 @@ void oracle_hot_start(oracle_lattice *L, uint64_t seed)
             put_link(L, s, mu, &u);
         }
     }
+    set_frozen_links(L);
     L->sweep = 0;
     L->exhausted = 0;
 }
@@ -716,6 +765,7 @@ void oracle_reunitarize(oracle_lattice *L)
 #pragma omp parallel for schedule(static)
     for (long s = 0; s < L->V; ++s)
         for (int mu = 0; mu < 4; ++mu) {
+            if (is_frozen(L, s, mu)) continue;
             mat u = get_link(L, s, mu);
             mat r = reunitarize_one(L->N, &u);
             put_link(L, s, mu, &r);

@@ -31,6 +31,9 @@ extern "C" {
 typedef struct oracle_lattice oracle_lattice;
 
 enum { ORACLE_HEATBATH = 0, ORACLE_OVERRELAX = 1 };
+/* Where the background field lives: as a phase on every dynamical y-link
+ * (effective links U B), or on the frozen spatial links of the t = 0 slice. */
+enum { ORACLE_FIELD_LINKS = 0, ORACLE_FIELD_FROZEN = 1 };
 
 /* Philox-4x32-10 block function (Salmon et al., SC11).  ctr[4], key[2] in,
  * out[4] out. */
@@ -45,6 +48,8 @@ double oracle_uniform(uint32_t w);
  * allocation failure. */
 oracle_lattice *oracle_create(int N, int Ns, int Nt, double beta, int flux,
                               int nhit, uint32_t lattice_id);
+oracle_lattice *oracle_create_ex(int N, int Ns, int Nt, double beta, int flux,
+                                 int nhit, uint32_t lattice_id, int field_mode);
 void oracle_destroy(oracle_lattice *L);
 void oracle_set_threads(int n);
 int oracle_get_threads(void);
