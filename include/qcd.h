@@ -64,6 +64,18 @@ extern "C" {
 /* Start. */
 #define QCD_COLD 0 /* every link the unit matrix                             */
 #define QCD_HOT 1  /* every link Haar-random: SU(2) Shoemake, SU(3) Mezzadri */
+/* Field modes (sec. 1: lattice gauge theory in an external chromomagnetic
+ * field; the paper gives no formula, so both are readings of that claim).
+ * B_y(x) = diag(e^{i phi}, e^{-i phi} [, 1]), phi = 2 pi n x / Ns^2 along
+ * lambda3 (sigma3 for SU(2)); B = 1 on x-, z- and t-links. */
+#define QCD_FIELD_LINKS 0  /* effective links U B on every link: updates and
+                              measurements act on U B, U = (U B)_new B^+ is
+                              stored (a change of variables of the n = 0
+                              theory for the effective-link observables)     */
+#define QCD_FIELD_FROZEN 1 /* the spatial links of the time slice t = 0 are
+                              set to B and never updated nor reunitarized;
+                              every other link carries no phase (fixed-
+                              boundary background field, physically visible) */
 /* Update kinds for qcd_phase. */
 #define QCD_HEATBATH 0
 #define QCD_OVERRELAX 1
@@ -86,7 +98,18 @@ typedef struct qcd_lattice qcd_lattice;
 int qcd_lattice_create(qcd_lattice **out, int group, int Ns, int Nt,
                        double beta, int flux, int precision, int start,
                        uint64_t seed, void *stream);
+/* As qcd_lattice_create with an explicit field mode (QCD_FIELD_LINKS or
+ * QCD_FIELD_FROZEN; anything else is QCD_ERR_INVALID_ARG).  In the frozen
+ * mode the start is applied to every link and then the t = 0 spatial links are
+ * overwritten with B; qcd_set_links stores what it is given, frozen links
+ * included (a checkpoint holds them as B).  qcd_lattice_create is this call
+ * with QCD_FIELD_LINKS. */
+int qcd_lattice_create_ex(qcd_lattice **out, int group, int Ns, int Nt,
+                          double beta, int flux, int field_mode, int precision,
+                          int start, uint64_t seed, void *stream);
 int qcd_lattice_destroy(qcd_lattice *lat);
+/* The field mode the lattice was created with. */
+int qcd_get_field_mode(qcd_lattice *lat, int *field_mode);
 
 /* Cap on Kennedy-Pendleton tries per (link, subgroup); >= 1.  When every try
  * is rejected the SU(2) link is kept and the SU(3) subgroup step is skipped

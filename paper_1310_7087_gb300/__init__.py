@@ -29,6 +29,8 @@ QCD_COLD = 0
 QCD_HOT = 1
 QCD_HEATBATH = 0
 QCD_OVERRELAX = 1
+QCD_FIELD_LINKS = 0
+QCD_FIELD_FROZEN = 1
 
 # Every symbol include/qcd.h declares, with ctypes (restype, argtypes).
 _vp, _i, _d, _u32, _u64, _sz = (ctypes.c_void_p, ctypes.c_int, ctypes.c_double,
@@ -36,7 +38,9 @@ _vp, _i, _d, _u32, _u64, _sz = (ctypes.c_void_p, ctypes.c_int, ctypes.c_double,
 _P = ctypes.POINTER
 SIGNATURES = {
     "qcd_lattice_create": (_i, [_P(_vp), _i, _i, _i, _d, _i, _i, _i, _u64, _vp]),
+    "qcd_lattice_create_ex": (_i, [_P(_vp), _i, _i, _i, _d, _i, _i, _i, _i, _u64, _vp]),
     "qcd_lattice_destroy": (_i, [_vp]),
+    "qcd_get_field_mode": (_i, [_vp, _P(_i)]),
     "qcd_set_nhit": (_i, [_vp, _i]),
     "qcd_sweep": (_i, [_vp, _i, _i, _u64]),
     "qcd_phase": (_i, [_vp, _i, _i, _i, _u64]),
@@ -128,6 +132,21 @@ def qcd_lattice_create(group, Ns, Nt, beta, flux=0, precision=QCD_FP32_COMPRESSE
     _check(lib().qcd_lattice_create(ctypes.byref(h), group, Ns, Nt, beta, flux, precision,
                                     start, seed, _stream_handle(stream)))
     return h
+
+
+def qcd_lattice_create_ex(group, Ns, Nt, beta, flux=0, field_mode=QCD_FIELD_LINKS,
+                          precision=QCD_FP32_COMPRESSED, start=QCD_HOT, seed=1,
+                          stream=None) -> ctypes.c_void_p:
+    h = ctypes.c_void_p()
+    _check(lib().qcd_lattice_create_ex(ctypes.byref(h), group, Ns, Nt, beta, flux, field_mode,
+                                       precision, start, seed, _stream_handle(stream)))
+    return h
+
+
+def qcd_get_field_mode(h) -> int:
+    v = ctypes.c_int()
+    _check(lib().qcd_get_field_mode(h, ctypes.byref(v)))
+    return v.value
 
 
 def qcd_lattice_destroy(h) -> None:
@@ -361,11 +380,13 @@ class Lattice:
     """Owning wrapper around one ``qcd_lattice`` handle."""
 
     def __init__(self, group, Ns, Nt, beta, flux=0, precision=QCD_FP32_COMPRESSED,
-                 start=QCD_HOT, seed=1, stream=None, nhit=10):
+                 start=QCD_HOT, seed=1, stream=None, nhit=10, field_mode=QCD_FIELD_LINKS):
         self.group, self.Ns, self.Nt = group, Ns, Nt
         self.V = Ns ** 3 * Nt
         self.beta, self.flux, self.precision, self.seed = beta, flux, precision, seed
-        self.h = qcd_lattice_create(group, Ns, Nt, beta, flux, precision, start, seed, stream)
+        self.field_mode = field_mode
+        self.h = qcd_lattice_create_ex(group, Ns, Nt, beta, flux, field_mode, precision, start,
+                                       seed, stream)
         if nhit != 10:
             qcd_set_nhit(self.h, nhit)
 
@@ -431,6 +452,7 @@ class Lattice:
         self.V = Ns ** 3 * Nt
         self.beta, self.flux, self.precision, self.seed = beta, flux, precision, seed
         self.h = qcd_lattice_load(path, precision, stream)
+        self.field_mode = qcd_get_field_mode(self.h)
         return self
 
     @property

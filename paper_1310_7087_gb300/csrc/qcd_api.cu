@@ -94,6 +94,7 @@ void tune_store_locked() {
 struct qcd_lattice {
   const qcd::PolicyOps* ops = nullptr;
   int group = 0, precision = 0, Ns = 0, Nt = 0, flux = 0, nhit = 10;
+  int field_mode = QCD_FIELD_LINKS;
   double beta = 0.0;
   uint64_t seed = 0;
   uint32_t lattice_id = 0;
@@ -145,6 +146,7 @@ qcd::Ctx make_ctx(const qcd_lattice* L, uint64_t seed) {
   a.sweep_rw = L->d_sweep;
   a.nhit = L->nhit;
   a.flux = L->flux;
+  a.field_mode = L->field_mode;
   a.phase64 = L->d_phase64;
   a.phase32 = L->d_phase32;
   a.exhausted = L->d_exhausted;
@@ -274,7 +276,8 @@ std::string tune_key(const qcd_lattice* L) {
       if (ch == ' ') ch = '_';
   }
   char buf[256];
-  snprintf(buf, sizeof buf, "su%d_p%d_%dx%d_f%d_%s", L->group, L->precision, L->Ns, L->Nt, L->flux != 0 ? 1 : 0,
+  snprintf(buf, sizeof buf, "su%d_p%d_%dx%d_f%d_%s", L->group, L->precision, L->Ns, L->Nt,
+           L->flux != 0 && L->field_mode == QCD_FIELD_LINKS ? 1 : 0,
            dev.c_str());
   return buf;
 }
@@ -363,8 +366,15 @@ const char* qcd_last_error(void) { return g_last_error.c_str(); }
 
 int qcd_lattice_create(qcd_lattice** out, int group, int Ns, int Nt, double beta, int flux, int precision,
                        int start, uint64_t seed, void* stream) {
+  return qcd_lattice_create_ex(out, group, Ns, Nt, beta, flux, QCD_FIELD_LINKS, precision, start, seed, stream);
+}
+
+int qcd_lattice_create_ex(qcd_lattice** out, int group, int Ns, int Nt, double beta, int flux, int field_mode,
+                          int precision, int start, uint64_t seed, void* stream) {
   if (!out) return set_error(QCD_ERR_INVALID_ARG, "out is null");
   *out = nullptr;
+  if (field_mode != QCD_FIELD_LINKS && field_mode != QCD_FIELD_FROZEN)
+    return set_error(QCD_ERR_INVALID_ARG, "unknown field mode %d", field_mode);
   if (group != 2 && group != 3) return set_error(QCD_ERR_INVALID_ARG, "group must be 2 or 3, got %d", group);
   if (Ns < 2 || Nt < 2 || (Ns & 1) || (Nt & 1))
     return set_error(QCD_ERR_INVALID_ARG, "Ns and Nt must be even and >= 2 (got %d, %d)", Ns, Nt);
@@ -383,6 +393,7 @@ int qcd_lattice_create(qcd_lattice** out, int group, int Ns, int Nt, double beta
   L->Ns = Ns;
   L->Nt = Nt;
   L->flux = flux;
+  L->field_mode = field_mode;
   L->beta = beta;
   L->seed = seed;
   L->stream = static_cast<cudaStream_t>(stream);
@@ -417,9 +428,18 @@ int qcd_lattice_create(qcd_lattice** out, int group, int Ns, int Nt, double beta
     return fail(set_error(QCD_ERR_CUDA, "phase table: %s", cudaGetErrorString(e)));
   if ((e = L->ops->start(make_ctx(L, seed), start, L->stream)) != cudaSuccess)
     return fail(set_error(QCD_ERR_CUDA, "start: %s", cudaGetErrorString(e)));
+  if (field_mode == QCD_FIELD_FROZEN && (e = L->ops->set_frozen(make_ctx(L, seed), L->stream)) != cudaSuccess)
+    return fail(set_error(QCD_ERR_CUDA, "frozen links: %s", cudaGetErrorString(e)));
   if ((e = cudaStreamSynchronize(L->stream)) != cudaSuccess)
     return fail(set_error(QCD_ERR_CUDA, "create: %s", cudaGetErrorString(e)));
   *out = L;
+  return QCD_OK;
+}
+
+int qcd_get_field_mode(qcd_lattice* L, int* field_mode) {
+  if (int rc = check(L)) return rc;
+  if (!field_mode) return set_error(QCD_ERR_INVALID_ARG, "field_mode is null");
+  *field_mode = L->field_mode;
   return QCD_OK;
 }
 
@@ -648,7 +668,7 @@ struct CheckpointHeader {
   char magic[8];
   uint32_t version, group, precision, Ns, Nt;
   int32_t flux;
-  uint32_t nhit, lattice_id, sweep, pad;
+  uint32_t nhit, lattice_id, sweep, field_mode;  // field_mode 0 in files written before the mode existed
   uint64_t seed;
   double beta;
   uint64_t exhausted;
@@ -668,6 +688,7 @@ int qcd_save(qcd_lattice* L, const char* path) {
   h.Ns = uint32_t(L->Ns);
   h.Nt = uint32_t(L->Nt);
   h.flux = L->flux;
+  h.field_mode = uint32_t(L->field_mode);
   h.nhit = uint32_t(L->nhit);
   h.lattice_id = L->lattice_id;
   h.seed = L->seed;
@@ -696,13 +717,13 @@ int qcd_lattice_load(qcd_lattice** out, const char* path, int precision, void* s
   CheckpointHeader h{};
   uint64_t pad8 = 0;
   if (fread(&h, sizeof h, 1, f) != 1 || fread(&pad8, 8, 1, f) != 1 || std::memcmp(h.magic, kMagic, 8) != 0 ||
-      h.version != 1 || (h.group != 2 && h.group != 3) || h.Ns < 2 || h.Nt < 2 || h.Ns > 1290 || h.Nt > (1u << 30)) {
+      h.version != 1 || (h.group != 2 && h.group != 3) || h.field_mode > 1 || h.Ns < 2 || h.Nt < 2 || h.Ns > 1290 || h.Nt > (1u << 30)) {
     fclose(f);
     return set_error(QCD_ERR_INVALID_ARG, "%s is not a version-1 checkpoint", path);
   }
   qcd_lattice* L = nullptr;
-  int rc = qcd_lattice_create(&L, int(h.group), int(h.Ns), int(h.Nt), h.beta, h.flux, precision, QCD_COLD, h.seed,
-                              stream);
+  int rc = qcd_lattice_create_ex(&L, int(h.group), int(h.Ns), int(h.Nt), h.beta, h.flux, int(h.field_mode),
+                                 precision, QCD_COLD, h.seed, stream);
   if (rc) {
     fclose(f);
     return rc;

@@ -24,6 +24,8 @@ struct Ctx {
   uint32_t* sweep_rw;           // same counter, for the end-of-sweep advance
   int nhit;
   int flux;                     // 0: no background field
+  int field_mode;               // 0: phase on every y-link (effective links U B);
+                                // 1: field on the frozen spatial links of t = 0
   const double2* phase64;       // per x: (cos phi, sin phi), phi = 2 pi n x / Ns^2
   const float2* phase32;
   unsigned long long* exhausted;
@@ -53,10 +55,15 @@ struct PolicyOps {
   cudaError_t (*measure)(const Ctx&, int effective, cudaStream_t);
   cudaError_t (*to_canonical)(const Ctx&, double* dev_out, cudaStream_t);
   cudaError_t (*from_canonical)(const Ctx&, const double* dev_in, cudaStream_t);
+  // Frozen-boundary mode: set the spatial links of the t = 0 slice to B.
+  cudaError_t (*set_frozen)(const Ctx&, cudaStream_t);
   // Largest block the phase kernels of this storage can launch with (the
   // minimum over heat-bath / overrelaxation, with and without the field).
   int (*max_phase_block)();
 };
+
+// Effective-link phases are applied only in field mode 0 with a field.
+inline bool phases_on_links(const Ctx& a) { return a.flux != 0 && a.field_mode == 0; }
 
 // Record the message returned by qcd_last_error() on this thread; returns code.
 int set_last_error(int code, const char* msg);

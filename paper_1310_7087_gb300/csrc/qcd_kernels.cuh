@@ -260,12 +260,18 @@ __device__ __forceinline__ void left_rotate(M3<R>& m, const Quat<R>& r, int i, i
 #define QCD_SU3_PHASE_MAXNREG 96
 #endif
 
+// Frozen-boundary mode: the spatial links of the t = 0 slice are not updated.
+__device__ __forceinline__ bool frozen_link(const Ctx& a, int mu, int t) {
+  return a.field_mode == 1 && mu < 3 && t == 0;
+}
+
 template <typename R, bool FIELD, int KIND>
 __global__ void __maxnreg__(QCD_SU3_PHASE_MAXNREG) su3_phase_kernel(const Ctx a, int parity, int mu) {
   using P = SU3Policy<R>;
   const int h = blockIdx.x * blockDim.x + threadIdx.x;
   if (h >= a.g.Vh) return;
   const Site x = site_of(a.g, parity, h);
+  if (frozen_link(a, mu, x.t)) return;
   const M3<R> A = staple<P, FIELD>(a, x, mu);
   M3<R> U = P::load(a.links, a.g, mu, parity, h);
   M3<R> Ut = U;
@@ -384,6 +390,7 @@ __global__ void su2_reunit_kernel(const Ctx a, int advance) {
   const int64_t idx = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
   if (idx >= 8LL * a.g.Vh) return;
   const int plane = int(idx / a.g.Vh), h = int(idx % a.g.Vh);
+  if (a.field_mode == 1 && frozen_link(a, plane >> 1, site_of(a.g, plane & 1, h).t)) return;
   su2_reunit_link<R>(a, plane >> 1, plane & 1, h);
 }
 
@@ -487,6 +494,7 @@ __global__ void su3_reunit_kernel(const Ctx a, int advance) {
   const int64_t idx = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
   if (idx >= 8LL * a.g.Vh) return;
   const int plane = int(idx / a.g.Vh), h = int(idx % a.g.Vh);
+  if (a.field_mode == 1 && frozen_link(a, plane >> 1, site_of(a.g, plane & 1, h).t)) return;
   su3_reunit_link<R>(a, plane >> 1, plane & 1, h);
 }
 
@@ -565,6 +573,34 @@ __global__ void start_kernel(const Ctx a, int hot) {
       for (int c = 0; c < 3; ++c) u.e[r][c] = {R(m.e[r][c].re), R(m.e[r][c].im)};
   }
   P::store(a.links, a.g, mu, par, h, u);
+}
+
+// Frozen-boundary mode: the spatial links of the t = 0 slice hold B (y-links
+// diag(e^{i phi}, e^{-i phi} [,1]), x- and z-links unity).
+template <class P>
+__global__ void set_frozen_kernel(const Ctx a) {
+  using R = typename P::Real;
+  const int64_t idx = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  const int64_t V3 = int64_t(a.g.Ns) * a.g.Ns * a.g.Ns;
+  if (idx >= 3 * V3) return;
+  const int mu = int(idx / V3), s = int(idx % V3);  // t = 0: s is the spatial index
+  const Site x{s % a.g.Ns, (s / a.g.Ns) % a.g.Ns, s / (a.g.Ns * a.g.Ns), 0};
+  double c = 1.0, sn = 0.0;
+  if (mu == 1) {
+    const double2 ph = a.phase64[x.x];
+    c = ph.x;
+    sn = ph.y;
+  }
+  typename P::Link u;
+  if constexpr (P::N == 2) {
+    u = {R(c), R(0), R(0), R(sn)};
+  } else {
+    m3_zero(u);
+    u.e[0][0] = {R(c), R(sn)};
+    u.e[1][1] = {R(c), R(-sn)};
+    u.e[2][2] = {R(1), R(0)};
+  }
+  P::store(a.links, a.g, mu, parity_of(x), lex(a.g, x) >> 1, u);
 }
 
 // ---------------------------------------------------------------------------
@@ -769,7 +805,7 @@ inline void launch_phase_t(const Ctx& a, int parity, int mu, int block, cudaStre
 
 template <class P>
 cudaError_t launch_phase(const Ctx& a, int kind, int parity, int mu, int block, cudaStream_t st) {
-  const bool field = a.flux != 0;
+  const bool field = phases_on_links(a);
   if (kind == KIND_HB) {
     if (field) launch_phase_t<P, true, KIND_HB>(a, parity, mu, block, st);
     else launch_phase_t<P, false, KIND_HB>(a, parity, mu, block, st);
@@ -798,9 +834,16 @@ cudaError_t launch_start(const Ctx& a, int hot, cudaStream_t st) {
 }
 
 template <class P>
+cudaError_t launch_set_frozen(const Ctx& a, cudaStream_t st) {
+  const int64_t n = 3LL * a.g.Ns * a.g.Ns * a.g.Ns;
+  set_frozen_kernel<P><<<grid_for(n, 256), 256, 0, st>>>(a);
+  return cudaGetLastError();
+}
+
+template <class P>
 cudaError_t launch_measure(const Ctx& a, int effective, cudaStream_t st) {
   const int np = meas_plaq_blocks(a.g), nl = meas_poly_blocks(a.g);
-  if (effective && a.flux != 0)
+  if (effective && phases_on_links(a))
     measure_kernel<P, true><<<np + nl, MEAS_THREADS, 0, st>>>(a, np);
   else
     measure_kernel<P, false><<<np + nl, MEAS_THREADS, 0, st>>>(a, np);
@@ -847,6 +890,7 @@ constexpr PolicyOps make_ops(int precision) {
                    &launch_measure<P>,
                    &launch_to_canonical<P>,
                    &launch_from_canonical<P>,
+                   &launch_set_frozen<P>,
                    &max_phase_block<P>};
 }
 

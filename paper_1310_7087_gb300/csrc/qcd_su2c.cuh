@@ -62,6 +62,7 @@ template <typename R, bool FIELD, int KIND, int MU, bool CG>
 __device__ __forceinline__ void su2c_update(const Ctx& a, int parity, int h, uint32_t sweep) {
   using P = SU2Policy<R>;
   const LexSite x = lex_site(a, parity, h);
+  if (frozen_link(a, MU, x.c[3])) return;
   const Quat<R> A = su2c_staple<R, FIELD, MU, CG>(a, parity, x);
   const R k2 = qnorm2(A);
   constexpr bool phased = FIELD && MU == 1;
@@ -114,7 +115,7 @@ inline void su2c_launch_kind(const Ctx& a, int parity, int mu, int block, cudaSt
 
 template <typename R>
 cudaError_t su2c_launch_phase(const Ctx& a, int kind, int parity, int mu, int block, cudaStream_t st) {
-  const bool field = a.flux != 0;
+  const bool field = phases_on_links(a);
   if (kind == KIND_HB) {
     if (field) su2c_launch_kind<R, true, KIND_HB>(a, parity, mu, block, st);
     else su2c_launch_kind<R, false, KIND_HB>(a, parity, mu, block, st);
@@ -156,6 +157,7 @@ PolicyOps su2c_ops(int precision) {
                    &launch_measure<P>,
                    &launch_to_canonical<P>,
                    &launch_from_canonical<P>,
+                   &launch_set_frozen<P>,
                    &su2c_max_phase_block<R>};
 }
 

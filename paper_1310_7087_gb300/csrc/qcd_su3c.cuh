@@ -218,6 +218,7 @@ __global__ void __maxnreg__(QCD_SU3_PHASE_MAXNREG) su3c_phase_kernel(const Ctx a
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= a.g.Vh) return;
   const LexSite x = lex_site_ytz(a.g, parity, i);
+  if (frozen_link(a, MU, x.c[3])) return;
   const int h = x.s >> 1;
   const M3<float> A = su3c_staple<FIELD, MU>(a, parity, x);
   su3c_update<FIELD, KIND, MU>(a, parity, h, x, A, su3c_full(su3c_load(a.links, a.g, MU, parity, h)));
@@ -240,7 +241,7 @@ inline void su3c_launch_kind(const Ctx& a, int parity, int mu, int block, cudaSt
 }
 
 inline cudaError_t su3c_launch_phase(const Ctx& a, int kind, int parity, int mu, int block, cudaStream_t st) {
-  const bool field = a.flux != 0;
+  const bool field = phases_on_links(a);
   if (kind == KIND_HB) {
     if (field) su3c_launch_kind<true, KIND_HB>(a, parity, mu, block, st);
     else su3c_launch_kind<false, KIND_HB>(a, parity, mu, block, st);
