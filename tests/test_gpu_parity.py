@@ -52,6 +52,42 @@ def check_links(a, b, precision, what=""):
     return err
 
 
+def phase_mask(Ns, Nt, parity, mu):
+    """Links a checkerboard phase (parity, mu) updates, in the canonical order
+    [t][z][y][x][mu]."""
+    t, z, y, x = np.meshgrid(*(np.arange(n) for n in (Nt, Ns, Ns, Ns)), indexing="ij")
+    on = ((x + y + z + t) & 1).reshape(-1) == parity
+    m = np.zeros((on.size, 4), dtype=bool)
+    m[on, mu] = True
+    return m.reshape(-1)
+
+
+class FP32Tally:
+    """FP32 bar pooled over the kernels of one schedule: links outside a phase
+    bit-identical, at least 99.99 % of updated links within 1e-5 of the oracle
+    (one such link is always allowed: a 4^3 x 4 schedule has only 6144
+    updates), none beyond 1e-4.  An overrelaxation reflection divides by the
+    norm of the subgroup block, so the rare links where that norm is small
+    amplify FP32 rounding past 1e-5 (about one update in 10^5, in any FP32
+    evaluation order)."""
+
+    def __init__(self):
+        self.n = self.bad = 0
+        self.worst = 0.0
+
+    def add(self, got, ref, mask, what):
+        err = link_err(got, ref)
+        assert err[~mask].max(initial=0.0) == 0.0, (what, "link outside the phase changed")
+        e = err[mask]
+        self.n += e.size
+        self.bad += int((e > 1e-5).sum())
+        self.worst = max(self.worst, float(e.max(initial=0.0)))
+        assert self.worst < 1e-4, (what, self.worst)
+
+    def check(self):
+        assert self.bad <= max(1.0, 1e-4 * self.n), (self.bad, self.n, self.worst)
+
+
 # (group, precision, Ns, Nt, beta, flux): several tiles, ragged tails (Vh = 432,
 # 216), the degenerate 2^4 lattice, field on and off.
 CASES = [
@@ -118,16 +154,23 @@ def run_kernel_by_kernel(q, case, seed=7):
     schedule = [(q.QCD_HEATBATH, p, mu) for p in (0, 1) for mu in range(4)]
     schedule += [(q.QCD_OVERRELAX, p, mu) for _ in range(n_or) for p in (0, 1) for mu in range(4)]
     schedule += [("reunitarize", 0, 0)]
+    tally = FP32Tally()
     for kind, parity, mu in schedule:
         orc.set_links(lat.get_links())
         orc.sweep_counter = lat.sweep_counter
         if kind == "reunitarize":
             lat.reunitarize()
             orc.reunitarize()
+            mask = np.ones(lat.V * 4, dtype=bool)
         else:
             lat.phase(kind, parity, mu, seed)
             orc.phase(kind, parity, mu, seed)
-        check_links(lat.get_links(), orc.get_links(), case[1], (kind, parity, mu))
+            mask = phase_mask(case[2], case[3], parity, mu)
+        if case[1] == FP64_PLAIN:
+            check_links(lat.get_links(), orc.get_links(), case[1], (kind, parity, mu))
+        else:
+            tally.add(lat.get_links(), orc.get_links(), mask, (kind, parity, mu))
+    tally.check()
     lat.close()
 
 
@@ -159,6 +202,7 @@ def test_measurements_on_one_configuration(q, case):
 def test_every_single_phase(q, case):
     lat, orc = pair(q, case)
     lat.sweep(1, 1, 3)
+    tally = FP32Tally()
     for kind in (q.QCD_HEATBATH, q.QCD_OVERRELAX):
         for parity in (0, 1):
             for mu in range(4):
@@ -166,7 +210,12 @@ def test_every_single_phase(q, case):
                 orc.sweep_counter = lat.sweep_counter
                 lat.phase(kind, parity, mu, 21)
                 orc.phase(kind, parity, mu, 21)
-                check_links(lat.get_links(), orc.get_links(), case[1], (kind, parity, mu))
+                if case[1] == FP64_PLAIN:
+                    check_links(lat.get_links(), orc.get_links(), case[1], (kind, parity, mu))
+                else:
+                    tally.add(lat.get_links(), orc.get_links(), phase_mask(case[2], case[3], parity, mu),
+                              (kind, parity, mu))
+    tally.check()
     lat.close()
 
 
