@@ -1,11 +1,12 @@
-"""FP64 CPU oracle for the checkerboard SU(2)/SU(3) gauge sweep.
+"""FP64 CPU oracle for the checkerboard SU(2)/SU(3) gauge sweep and for the
+O(N) model sweep by multi-hit Metropolis.
 
 TEST INFRASTRUCTURE.  Only ``tests/``, ``__graft_entry__.smoke()`` and the
 CPU-baseline leg of ``bench.py`` may import this package.  The product path
 (the CUDA library and its binding) never imports it, and this package never
 imports the product path.  The arithmetic lives in ``qcd_oracle.c`` (plain C,
-FP64, full N x N complex matrices); this module only compiles it with gcc and
-marshals arguments through ctypes.
+FP64, full N x N complex matrices) and ``on_oracle.c`` (the O(N) model); this
+module only compiles them with gcc and marshals arguments through ctypes.
 """
 from __future__ import annotations
 
@@ -17,7 +18,8 @@ import sys
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-_SRC = os.path.join(_HERE, "qcd_oracle.c")
+_SRCS = [os.path.join(_HERE, f) for f in ("qcd_oracle.c", "on_oracle.c")]
+_HDRS = [os.path.join(_HERE, f) for f in ("qcd_oracle.h", "on_oracle.h")]
 _LIB = os.path.join(_HERE, "liboracle.so")
 
 HEATBATH = 0
@@ -34,11 +36,10 @@ CFLAGS = ["-O2", "-std=c11", "-fopenmp", "-fPIC", "-shared",
 def build(force: bool = False) -> str:
     """Compile ``liboracle.so`` next to its source (skipped when up to date)."""
     if (not force and os.path.exists(_LIB)
-            and os.path.getmtime(_LIB) >= max(os.path.getmtime(_SRC),
-                                               os.path.getmtime(os.path.join(_HERE, "qcd_oracle.h")))):
+            and os.path.getmtime(_LIB) >= max(os.path.getmtime(f) for f in _SRCS + _HDRS)):
         return _LIB
     tmp = _LIB + ".%d.tmp" % os.getpid()
-    cmd = ["gcc", *CFLAGS, "-o", tmp, _SRC, "-lm"]
+    cmd = ["gcc", *CFLAGS, "-o", tmp, *_SRCS, "-lm"]
     subprocess.run(cmd, check=True)
     os.replace(tmp, _LIB)
     return _LIB
@@ -88,6 +89,27 @@ def lib() -> ctypes.CDLL:
         L.oracle_kp_samples.argtypes = [d, i, u64, l, P(d), P(i)]
         L.oracle_su2_samples.argtypes = [d, i, u64, l, P(d)]
         L.oracle_haar_samples.argtypes = [i, u64, l, P(d)]
+        L.on_create.argtypes = [i, i, i, d, d, d, i, u32]
+        L.on_create.restype = vp
+        L.on_destroy.argtypes = [vp]
+        L.on_cold_start.argtypes = [vp]
+        L.on_hot_start.argtypes = [vp, u64]
+        L.on_phase.argtypes = [vp, i, u64]
+        L.on_sweep.argtypes = [vp, i, u64]
+        L.on_site_update.argtypes = [vp, l, u64, P(d)]
+        L.on_site_update.restype = i
+        L.on_local_action.argtypes = [vp, l, P(d)]
+        L.on_local_action.restype = d
+        L.on_action.argtypes = [vp]
+        L.on_action.restype = d
+        L.on_measure.argtypes = [vp, P(d)]
+        L.on_get_field.argtypes = [vp, P(d)]
+        L.on_set_field.argtypes = [vp, P(d)]
+        L.on_get_sweep.argtypes = [vp]
+        L.on_get_sweep.restype = u32
+        L.on_set_sweep.argtypes = [vp, u32]
+        L.on_accepted.argtypes = [vp]
+        L.on_accepted.restype = ctypes.c_longlong
         _lib = L
     return _lib
 
@@ -226,6 +248,84 @@ class OracleLattice:
         out = np.zeros((self.N, self.N, 2), np.float64)
         ex = lib().oracle_link_update(self._h, kind, s, mu, seed, _dptr(out))
         return out[..., 0] + 1j * out[..., 1], ex
+
+
+class OracleON:
+    """One O(N) model lattice held by the oracle, field in canonical order
+    ``[t][z][y][x][c]`` (x fastest), float64 of shape (V, N)."""
+
+    def __init__(self, N: int, Ns: int, Nt: int, kappa: float, lam: float, delta: float,
+                 nhit: int = 100, lattice_id: int = 0):
+        self.N, self.Ns, self.Nt = N, Ns, Nt
+        self.V = Ns ** 3 * Nt
+        self.kappa, self.lam, self.delta, self.nhit = kappa, lam, delta, nhit
+        h = lib().on_create(N, Ns, Nt, kappa, lam, delta, nhit, lattice_id)
+        if not h:
+            raise ValueError("on_create rejected the arguments")
+        self._h = h
+
+    def close(self) -> None:
+        if self._h:
+            lib().on_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def cold_start(self) -> None:
+        lib().on_cold_start(self._h)
+
+    def hot_start(self, seed: int) -> None:
+        lib().on_hot_start(self._h, seed)
+
+    def phase(self, parity: int, seed: int) -> None:
+        lib().on_phase(self._h, parity, seed)
+
+    def sweep(self, n: int, seed: int) -> None:
+        lib().on_sweep(self._h, n, seed)
+
+    def site_update(self, s: int, seed: int):
+        out = np.zeros(4, np.float64)
+        acc = lib().on_site_update(self._h, s, seed, _dptr(out))
+        return out[: self.N], acc
+
+    def local_action(self, s: int, phi) -> float:
+        p = np.zeros(4, np.float64)
+        p[: self.N] = phi
+        return lib().on_local_action(self._h, s, _dptr(p))
+
+    def action(self) -> float:
+        return lib().on_action(self._h)
+
+    def measure(self):
+        out = (ctypes.c_double * 7)()
+        lib().on_measure(self._h, out)
+        return list(out)
+
+    def get_field(self) -> np.ndarray:
+        out = np.zeros((self.V, self.N), np.float64)
+        lib().on_get_field(self._h, _dptr(out))
+        return out
+
+    def set_field(self, phi) -> None:
+        a = np.ascontiguousarray(phi, dtype=np.float64)
+        assert a.size == self.V * self.N
+        lib().on_set_field(self._h, _dptr(a))
+
+    @property
+    def sweep_counter(self) -> int:
+        return lib().on_get_sweep(self._h)
+
+    @sweep_counter.setter
+    def sweep_counter(self, v: int) -> None:
+        lib().on_set_sweep(self._h, v)
+
+    @property
+    def accepted(self) -> int:
+        return lib().on_accepted(self._h)
 
 
 def site_index(Ns: int, x: int, y: int, z: int, t: int) -> int:
