@@ -283,6 +283,36 @@ def run_batched(q, stream, world, rank, dist, sweeps):
     return out
 
 
+def run_on_model(q, stream):
+    """O(4) model, 32^4, NHIT = 100: seconds per working sweep (sweep +
+    measurement) in FP32 and FP64, as in the paper's Table 1."""
+    import torch
+    w = workloads.O4_32
+    out = {"workload": w.name, "unit": "site hits/s",
+           "sweep": "even + odd phase, %d Metropolis hits per site, then measurement" % w.nhit}
+    for prec, name in ((q.QCD_FP32_COMPRESSED, "f32"), (q.QCD_FP64_PLAIN, "f64")):
+        m = q.ONModel(w.N, w.L, w.L, w.kappa, w.lam, w.delta, prec, q.QCD_HOT, w.seed, stream, w.nhit)
+        m.sweep(2, w.seed)
+        m.measure()
+        torch.cuda.synchronize()
+        a0 = m.accepted
+        n = 10 if name == "f32" else 3
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(n):
+            m.sweep(1, w.seed)
+            m.measure()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / n
+        out[name] = {"ms_per_working_sweep": ms, "value": w.volume * w.nhit / (ms / 1e3),
+                     "acceptance": (m.accepted - a0) / (n * w.volume * w.nhit),
+                     "phi2": m.measure()[0]}
+        m.close()
+    out["paper_context"] = "Table 1, O(4) 32^4: GTX 560 Ti 0.72 s (single) / 0.99 s (double) per working sweep"
+    return out
+
+
 def main():
     args = parse()
     w = workloads.SU3_64x16
@@ -416,6 +446,7 @@ def main():
         lat64.close()
 
         extras["batched"] = run_batched(q, stream, world, rank, dist, workloads.batch_scan().sweeps)
+        extras["o4_model"] = run_on_model(q, stream)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:

@@ -278,6 +278,56 @@ int qcd_batch_set_wait(qcd_batch *b, double seconds);
  * -1 switches it off. */
 int qcd_batch_inject_stall(qcd_batch *b, int lattice);
 
+/* ------------------------------------------------------------------------
+ * O(N) model (sec. 3.3 "SUNCL and ONCL Modules": an N-vector field on the
+ * sites, checkerboard updates by an improved Metropolis algorithm; sec. 4,
+ * Table 1: O(4) with NHIT = 100 tries per site).  The paper gives no formula;
+ * readings:
+ *   action  S = sum_x [ -2 kappa sum_mu phi_x.phi_{x+mu} + phi_x.phi_x
+ *                       + lambda (phi_x.phi_x - 1)^2 ],  phi_x in R^N;
+ *   update  a visit of a site makes nhit Metropolis hits with the eight
+ *           neighbours fixed: hit h proposes phi' = phi + delta (2u - 1) per
+ *           component (Philox block (s, sweep, 3 << 4, h)) and accepts iff
+ *           dS <= 0 or u < exp(-dS), u = word h mod 4 of block
+ *           (s, sweep, 4 << 4, h / 4); key = (seed_lo, seed_hi);
+ *   sweep   even sites, then odd sites; the sweep counter advances once.
+ * Field storage on the device: one 16-byte vector per site (FP32 float4 or
+ * FP64 two double2), even/odd halves; canonical host order [s][c], N doubles
+ * per site, s = x + Ns (y + Ns (z + Ns t)).
+ * ------------------------------------------------------------------------ */
+typedef struct qcd_on qcd_on;
+
+/* N in 1..4; Ns, Nt even >= 2, Ns^3 Nt < 2^31; delta > 0; precision
+ * QCD_FP64_PLAIN (FP64 field and arithmetic) or QCD_FP32_COMPRESSED (FP32
+ * field and arithmetic, FP64 sums in measurements); start QCD_COLD
+ * (phi = (1, 0, .., 0)) or QCD_HOT (phi_c = 2u - 1 from Philox block
+ * (s, 0xFFFFFFFF, 2 << 4, 0)).  nhit defaults to 100.  Allocates the field
+ * (32 B per site FP32, 64 B FP64) and a few KB on the current device. */
+int qcd_on_create(qcd_on **out, int N, int Ns, int Nt, double kappa,
+                  double lambda, double delta, int precision, int start,
+                  uint64_t seed, void *stream);
+int qcd_on_destroy(qcd_on *m);
+int qcd_on_set_nhit(qcd_on *m, int nhit);
+/* Threads per block of the phase kernel: 64, 128 (default), 256 or 512. */
+int qcd_on_set_block(qcd_on *m, int threads);
+/* n_sweeps sweeps (one CUDA graph per sweep: even phase, odd phase, counter
+ * advance); seed is the Philox key of the call.  Stream-ordered. */
+int qcd_on_sweep(qcd_on *m, int n_sweeps, uint64_t seed);
+/* One checkerboard phase at the current sweep counter (no advance). */
+int qcd_on_phase(qcd_on *m, int parity, uint64_t seed);
+/* out[7] (host) = { <phi.phi>, (1/4V) sum_{x,mu} phi_x.phi_{x+mu}, |M|,
+ * M_0, M_1, M_2, M_3 },  M = (1/V) sum_x phi_x; FP64 sums in a fixed order.
+ * Synchronizes the stream. */
+int qcd_on_measure(qcd_on *m, double *out);
+/* Field in the canonical FP64 host layout (V N doubles); set rounds to the
+ * storage precision. */
+int qcd_on_get_field(qcd_on *m, double *host_out);
+int qcd_on_set_field(qcd_on *m, const double *host_in);
+int qcd_on_get_sweep(qcd_on *m, uint32_t *sweep);
+int qcd_on_set_sweep(qcd_on *m, uint32_t sweep);
+/* Accepted Metropolis hits since creation. */
+int qcd_on_get_accepted(qcd_on *m, unsigned long long *accepted);
+
 /* Message of the last failed call on this thread ("" if none). */
 const char *qcd_last_error(void);
 

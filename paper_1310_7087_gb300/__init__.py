@@ -73,6 +73,18 @@ SIGNATURES = {
     "qcd_batch_get_shape": (_i, [_vp, _P(_i), _P(_i)]),
     "qcd_batch_set_wait": (_i, [_vp, _d]),
     "qcd_batch_inject_stall": (_i, [_vp, _i]),
+    "qcd_on_create": (_i, [_P(_vp), _i, _i, _i, _d, _d, _d, _i, _i, _u64, _vp]),
+    "qcd_on_destroy": (_i, [_vp]),
+    "qcd_on_set_nhit": (_i, [_vp, _i]),
+    "qcd_on_set_block": (_i, [_vp, _i]),
+    "qcd_on_sweep": (_i, [_vp, _i, _u64]),
+    "qcd_on_phase": (_i, [_vp, _i, _u64]),
+    "qcd_on_measure": (_i, [_vp, _P(_d)]),
+    "qcd_on_get_field": (_i, [_vp, _P(_d)]),
+    "qcd_on_set_field": (_i, [_vp, _P(_d)]),
+    "qcd_on_get_sweep": (_i, [_vp, _P(_u32)]),
+    "qcd_on_set_sweep": (_i, [_vp, _u32]),
+    "qcd_on_get_accepted": (_i, [_vp, _P(ctypes.c_ulonglong)]),
     "qcd_last_error": (ctypes.c_char_p, []),
 }
 QCD_NOALLOC_SCRATCH_BYTES = 512 * 1024
@@ -462,3 +474,118 @@ class Lattice:
     @property
     def link_bytes(self):
         return qcd_link_bytes(self.h)
+
+
+# ---------------------------------------------------------------------------
+# O(N) model
+# ---------------------------------------------------------------------------
+def qcd_on_create(N, Ns, Nt, kappa, lam, delta, precision=QCD_FP32_COMPRESSED, start=QCD_HOT, seed=1,
+                  stream=None) -> ctypes.c_void_p:
+    h = ctypes.c_void_p()
+    _check(lib().qcd_on_create(ctypes.byref(h), N, Ns, Nt, kappa, lam, delta, precision, start, seed,
+                               _stream_handle(stream)))
+    return h
+
+
+def qcd_on_destroy(h) -> None:
+    _check(lib().qcd_on_destroy(h))
+
+
+def qcd_on_set_nhit(h, nhit: int) -> None:
+    _check(lib().qcd_on_set_nhit(h, nhit))
+
+
+def qcd_on_set_block(h, threads: int) -> None:
+    _check(lib().qcd_on_set_block(h, threads))
+
+
+def qcd_on_sweep(h, n_sweeps: int, seed: int) -> None:
+    _check(lib().qcd_on_sweep(h, n_sweeps, seed))
+
+
+def qcd_on_phase(h, parity: int, seed: int) -> None:
+    _check(lib().qcd_on_phase(h, parity, seed))
+
+
+def qcd_on_measure(h):
+    out = (ctypes.c_double * 7)()
+    _check(lib().qcd_on_measure(h, out))
+    return list(out)
+
+
+def qcd_on_get_field(h, V: int, N: int) -> np.ndarray:
+    out = np.zeros((V, N), np.float64)
+    _check(lib().qcd_on_get_field(h, _dptr(out)))
+    return out
+
+
+def qcd_on_set_field(h, phi) -> None:
+    a = np.ascontiguousarray(phi, dtype=np.float64)
+    _check(lib().qcd_on_set_field(h, _dptr(a)))
+
+
+def qcd_on_get_sweep(h) -> int:
+    v = ctypes.c_uint32()
+    _check(lib().qcd_on_get_sweep(h, ctypes.byref(v)))
+    return v.value
+
+
+def qcd_on_set_sweep(h, sweep: int) -> None:
+    _check(lib().qcd_on_set_sweep(h, sweep))
+
+
+def qcd_on_get_accepted(h) -> int:
+    v = ctypes.c_ulonglong()
+    _check(lib().qcd_on_get_accepted(h, ctypes.byref(v)))
+    return v.value
+
+
+class ONModel:
+    """Owning wrapper around one ``qcd_on`` handle (O(N) model, N <= 4)."""
+
+    def __init__(self, N, Ns, Nt, kappa, lam, delta, precision=QCD_FP32_COMPRESSED, start=QCD_HOT, seed=1,
+                 stream=None, nhit=100):
+        self.N, self.Ns, self.Nt = N, Ns, Nt
+        self.V = Ns ** 3 * Nt
+        self.kappa, self.lam, self.delta, self.precision, self.seed = kappa, lam, delta, precision, seed
+        self.h = qcd_on_create(N, Ns, Nt, kappa, lam, delta, precision, start, seed, stream)
+        if nhit != 100:
+            qcd_on_set_nhit(self.h, nhit)
+
+    def close(self):
+        if self.h:
+            qcd_on_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def sweep(self, n=1, seed=None):
+        qcd_on_sweep(self.h, n, self.seed if seed is None else seed)
+
+    def phase(self, parity, seed=None):
+        qcd_on_phase(self.h, parity, self.seed if seed is None else seed)
+
+    def measure(self):
+        return qcd_on_measure(self.h)
+
+    def get_field(self):
+        return qcd_on_get_field(self.h, self.V, self.N)
+
+    def set_field(self, phi):
+        qcd_on_set_field(self.h, phi)
+
+    @property
+    def sweep_counter(self):
+        return qcd_on_get_sweep(self.h)
+
+    @sweep_counter.setter
+    def sweep_counter(self, v):
+        qcd_on_set_sweep(self.h, v)
+
+    @property
+    def accepted(self):
+        return qcd_on_get_accepted(self.h)

@@ -203,10 +203,20 @@ __device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint32_t k0, uint32_t k1
   return c;
 }
 
-// ((w >> 9) + 1/2) 2^-23: a uniform in (0,1), exact in FP32 and FP64.
+// ((w >> 9) + 1/2) 2^-23: a uniform in (0,1), exact in FP32 and FP64.  Built
+// without an integer-to-float conversion (a slow pipe on this GPU): the 23
+// bits become the mantissa of x = 1 + m 2^-23 in [1, 2), and
+// x - (1 - 2^-24) = (2m + 1) 2^-24 is exact (at most 24 significant bits).
 template <typename R>
-__device__ __forceinline__ R u01(uint32_t w) {
-  return (R(w >> 9) + R(0.5)) * R(1.1920928955078125e-07);
+__device__ __forceinline__ R u01(uint32_t w);
+template <>
+__device__ __forceinline__ float u01<float>(uint32_t w) {
+  return __int_as_float(0x3F800000u | (w >> 9)) - 0.999999940395355224609375f;
+}
+template <>
+__device__ __forceinline__ double u01<double>(uint32_t w) {
+  return __longlong_as_double(0x3FF0000000000000ll | (static_cast<long long>(w >> 9) << 29)) -
+         0.999999940395355224609375;
 }
 
 enum : uint32_t { KIND_TRY = 0u, KIND_DIR = 1u, KIND_START = 2u };

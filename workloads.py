@@ -57,6 +57,30 @@ SU3_32x8 = tuple(Workload("su3_32^3x8_b6.0_n%d" % n, 3, 32, 8, 6.0, n, HOT, 3, 1
 SU3_64x16 = Workload("su3_64^3x16_b6.2_n1", 3, 64, 16, 6.2, 1, HOT, 5, 1, 4, 100)
 
 
+@dataclass(frozen=True)
+class ONWorkload:
+    """O(N) model run: lattice L^4, phi^4 couplings, Metropolis step delta,
+    NHIT hits per site visit."""
+    name: str
+    N: int
+    L: int
+    kappa: float
+    lam: float
+    delta: float
+    nhit: int = 100
+    seed: int = 7
+
+    @property
+    def volume(self) -> int:
+        return self.L ** 4
+
+
+# O(4) on 32^4 with NHIT = 100 (the paper's Table 1 O(4) setting and lattice);
+# kappa near the O(4) transition of the lambda = 1 model, delta for ~1/3 of
+# the hits accepted.
+O4_32 = ONWorkload("o4_32^4_k0.3_l1_nhit100", 4, 32, 0.3, 1.0, 0.8, 100, 7)
+
+
 @dataclass
 class BatchScan:
     """Batched parameter scan: independent SU(2) lattices of uneven sizes."""
