@@ -360,6 +360,18 @@ struct Dot2 {
 // u * (1 + d) rounded once: u + d u with d small.
 __device__ __forceinline__ float scale1p(float u, float d) { return fmaf(d, u, u); }
 
+// Near-unit norms: a Dot2 sum n = 1 + e with |e| small.  e = (s - 1) + c is
+// formed in FP32 (s - 1 exact for s in [1/2, 2]; one rounding, relative
+// 2^-24 of e), and (1 + e)^(-1/2) - 1 in FP64 by its series to e^3: for
+// |e| <= 2^-8 the dropped terms are below 35/128 e^4 < 7e-11, far below the
+// FP32 half-ulp of the corrected output.  Larger deviations take the full
+// FP64 square root.
+constexpr float REUNIT_SERIES_MAX = 0.00390625f;  // 2^-8
+__device__ __forceinline__ float dot2_excess(const Dot2& n) { return (n.s - 1.f) + n.c; }
+__device__ __forceinline__ double rsqrt1p_minus1(double e) {
+  return e * fma(e, fma(e, -0.3125, 0.375), -0.5);
+}
+
 template <typename R, bool CG = false>
 __device__ __forceinline__ void su2_reunit_link(const Ctx& a, int mu, int par, int h) {
   using P = SU2Policy<R>;
@@ -371,8 +383,9 @@ __device__ __forceinline__ void su2_reunit_link(const Ctx& a, int mu, int par, i
     n.add(u.q1, u.q1);
     n.add(u.q2, u.q2);
     n.add(u.q3, u.q3);
-    const double nn = n.value();
-    const float d = float(rsqrt_fp64(nn) - 1.0);
+    const float e = dot2_excess(n);
+    const float d = fabsf(e) <= REUNIT_SERIES_MAX ? float(rsqrt1p_minus1(double(e)))
+                                                  : float(rsqrt_fp64(n.value()) - 1.0);
     P::store(a.links, a.g, mu, par, h,
              Quat<R>{scale1p(u.q0, d), scale1p(u.q1, d), scale1p(u.q2, d), scale1p(u.q3, d)});
   } else {
@@ -415,14 +428,34 @@ __device__ __forceinline__ void su3f_reunit_rows(Cx<float> r[3], Cx<float> t[3])
     cim.add(r[k].re, t[k].im);  // Im conj(r) t = r.re t.im - r.im t.re
     cim.add(-r[k].im, t[k].re);
   }
-  const double N1 = n1.value(), M = m.value(), Cre = cre.value(), Cim = cim.value();
-  const double s1 = rsqrt_fp64(N1);
-  const double inv_n1 = s1 * s1;
-  const double qre = Cre * inv_n1, qim = Cim * inv_n1;
-  const double n2 = M - fma(Cre, qre, Cim * qim);
-  const double s2 = rsqrt_fp64(n2);
-  const float d1 = float(s1 - 1.0), d2 = float(s2 - 1.0);
-  const float bre = float(s2 * qre), bim = float(s2 * qim);  // s2 q
+  float d1, d2, bre, bim;
+  const float e1 = dot2_excess(n1), em = dot2_excess(m);
+  const float cr = cre.s + cre.c, ci = cim.s + cim.c;
+  if (fmaxf(fmaxf(fabsf(e1), fabsf(em)), fmaxf(fabsf(cr), fabsf(ci))) <= REUNIT_SERIES_MAX) {
+    // near-unitary rows (every sweep): series in the small FP64 quantities
+    // e1 = n1 - 1, em = m - 1, c;  1/n1 = 1 - e1 + e1^2 (error c e1^3),
+    // n2 - 1 = em - |c|^2 / n1
+    const double E1 = e1, EM = em, Cr = cr, Ci = ci;
+    const double w = fma(E1, E1 - 1.0, 1.0);
+    const double qre = Cr * w, qim = Ci * w;
+    const double E2 = fma(-Cr, qre, fma(-Ci, qim, EM));
+    const double D2 = rsqrt1p_minus1(E2);
+    d1 = float(rsqrt1p_minus1(E1));
+    d2 = float(D2);
+    bre = float(fma(D2, qre, qre));  // s2 q
+    bim = float(fma(D2, qim, qim));
+  } else {
+    const double N1 = n1.value(), M = m.value(), Cre = cre.value(), Cim = cim.value();
+    const double s1 = rsqrt_fp64(N1);
+    const double inv_n1 = s1 * s1;
+    const double qre = Cre * inv_n1, qim = Cim * inv_n1;
+    const double n2 = M - fma(Cre, qre, Cim * qim);
+    const double s2 = rsqrt_fp64(n2);
+    d1 = float(s1 - 1.0);
+    d2 = float(s2 - 1.0);
+    bre = float(s2 * qre);  // s2 q
+    bim = float(s2 * qim);
+  }
 #pragma unroll
   for (int k = 0; k < 3; ++k) {
     // row 2: t + (d2 t - b r), b = s2 q (complex)
