@@ -195,7 +195,54 @@ def cpu_baseline_oracle(w):
             "sample": "one HB pass, one OR pass, one reunitarization and one measurement of the full "
                       "%s lattice (%.1f s of CPU work), combined as 1 HB + %d OR per sweep"
                       % (w.name, sum(t.values()), w.n_or),
-            "seconds": {k: round(v, 3) for k, v in t.items()}}
+            "seconds": {k: round(v, 3) for k, v in t.items()},
+            "hb_lu_per_s": 4 * w.volume / t["hb"], "or_lu_per_s": 4 * w.volume / t["or"],
+            "sweeps_per_s": 1.0 / sweep_s, "cpu": cpu_model(), "plan": oracle_plan(oracle)}
+
+
+def cpu_model():
+    import platform
+    name = platform.processor() or platform.machine()
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                if line.lower().startswith(("model name", "cpu part")):
+                    name = "%s (%s)" % (platform.machine(), line.split(":", 1)[1].strip())
+                    break
+    except OSError:
+        pass
+    return {"model": name, "nproc": os.cpu_count()}
+
+
+def oracle_plan(oracle):
+    """Oracle timings on the small configurations (link updates/s, all host
+    cores unless noted): SU(2) 4^3x4 cold, 100 x (1 HB + 1 OR); SU(3) 16^3x4,
+    1 HB + 4 OR + reunitarization (also single-threaded); SU(2) and SU(3) 8^4,
+    sweeps of 1 HB + reunitarization without measurements, as in the paper's
+    8^4 comparison; SU(3) 32^3x8 two sweeps of 1 HB + 4 OR (a rate, so it
+    stands for a longer run)."""
+    def run(N, Ns, Nt, beta, n_hb_sweeps, n_or, seed, cold=False, threads=None):
+        n0 = oracle.get_threads()
+        if threads:
+            oracle.set_threads(threads)
+        try:
+            L = oracle.OracleLattice(N, Ns, Nt, beta, 0, 10, 0)
+            if not cold:
+                L.hot_start(seed)
+            t0 = time.perf_counter()
+            L.sweep(n_hb_sweeps, n_or, seed)
+            dt = time.perf_counter() - t0
+            L.close()
+        finally:
+            oracle.set_threads(n0)
+        lu = n_hb_sweeps * (1 + n_or) * 4 * Ns ** 3 * Nt
+        return {"lu_per_s": lu / dt, "seconds": round(dt, 3), "sweeps": n_hb_sweeps}
+    return {"su2_4^3x4_cold_100x(1HB+1OR)": run(2, 4, 4, 2.3, 100, 1, 1, cold=True),
+            "su3_16^3x4_1HB+4OR": run(3, 16, 4, 5.7, 1, 4, 7),
+            "su3_16^3x4_1HB+4OR_1thread": run(3, 16, 4, 5.7, 1, 4, 7, threads=1),
+            "su2_8^4_1HB": run(2, 8, 8, 2.3, 10, 0, 3),
+            "su3_8^4_1HB": run(3, 8, 8, 5.7, 4, 0, 3),
+            "su3_32^3x8_2x(1HB+4OR)": run(3, 32, 8, 6.0, 2, 4, 5)}
 
 
 def run_reference(args, w):
@@ -280,6 +327,38 @@ def run_batched(q, stream, world, rank, dist, sweeps):
            "launch": {"threads_per_cta": threads, "ctas": ctas}, "gpu_launches_per_call": 2,
            "mean_plaquette_last_sweep": float(bm[:, -1, 0].mean())}
     bt.close()
+    return out
+
+
+def run_paper_lattices(q, stream):
+    """Like-for-like context with the paper's Table 1 and its 8^4 comparison:
+    SU(2)/SU(3) 8^4 sweeps of 1 HB + reunitarization without measurement, and
+    SU(3) 32^4 working sweeps (1 HB + 4 OR + reunitarization + measurement),
+    FP32 and FP64.  These lattices fit in L2."""
+    import torch
+    runs = [("su2_8^4_sweep", 2, 8, 2.3, 0, False, "P: GTX 560 Ti 6e-4 s SP / 1e-3 s DP"),
+            ("su3_8^4_sweep", 3, 8, 5.7, 0, False, "P: GTX 560 Ti 1.3e-3 s SP / 4.9e-3 s DP"),
+            ("su3_32^4_working_sweep", 3, 32, 6.0, 4, True, "P: GTX 560 Ti 0.56 s SP / 1.17 s DP")]
+    out = {}
+    for name, group, L, beta, n_or, meas, paper in runs:
+        row = {"paper_context": paper}
+        for prec, pname in ((q.QCD_FP32_COMPRESSED, "f32"), (q.QCD_FP64_PLAIN, "f64")):
+            lat = q.Lattice(group, L, L, beta, 0, prec, q.QCD_HOT, 3, stream)
+            lat.sweep(2, n_or, 3)
+            torch.cuda.synchronize()
+            n = 20
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for _ in range(n):
+                q.qcd_sweep(lat.h, 1, n_or, 3)
+                if meas:
+                    q.qcd_measure(lat.h)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1) / n
+            row[pname] = {"s_per_sweep": ms / 1e3, "lu_per_s": (1 + n_or) * 4 * L ** 4 / (ms / 1e3)}
+            lat.close()
+        out[name] = row
     return out
 
 
@@ -395,6 +474,10 @@ def main():
                 "alg_bytes_per_launch": alg_bytes, "avg_launch_ms": per_launch_ms,
                 "kernel_ms": {n: round(m, 3) for n, m in zip(names, prof_ms)},
                 "kernel_launches": {n: int(c) for n, c in zip(names, prof_n)}}
+    # link updates per second of the heat-bath and overrelaxation kernels alone
+    # (V/2 updates per phase launch), whole job
+    rates = {k: world * (w.volume // 2) / (prof_ms[i] / max(1, prof_n[i]) / 1e3) if prof_n[i] else None
+             for k, i in (("hb", 0), ("or", 1))}
 
     # end to end through the C ABI: per step, the configuration comes from
     # pinned host memory and the measurement goes back to the host
@@ -447,6 +530,7 @@ def main():
 
         extras["batched"] = run_batched(q, stream, world, rank, dist, workloads.batch_scan().sweeps)
         extras["o4_model"] = run_on_model(q, stream)
+        extras["paper_lattices"] = run_paper_lattices(q, stream)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -462,6 +546,8 @@ def main():
                                parallelism="replicas" if world > 1 else "single GPU",
                                block=q.qcd_get_block(h)),
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks.summary(),
+                "hb_lu_per_s": rates["hb"], "or_lu_per_s": rates["or"],
+                "sweeps_per_s": 1e3 * args.steps / t_ms * world,
                 "gpu_launches": launches, "last_measurement": {"plaquette": last[0], "polyakov": last[1]},
                 **extras}
         print(json.dumps(line), flush=True)
