@@ -61,7 +61,7 @@ def lib() -> ctypes.CDLL:
         L.oracle_uniform.restype = d
         L.oracle_create.argtypes = [i, i, i, d, i, i, u32]
         L.oracle_create.restype = vp
-        L.oracle_create_ex.argtypes = [i, i, i, d, i, i, u32, i]
+        L.oracle_create_ex.argtypes = [i, i, i, d, i, i, i, u32, i]
         L.oracle_create_ex.restype = vp
         L.oracle_destroy.argtypes = [vp]
         L.oracle_set_threads.argtypes = [i]
@@ -165,11 +165,13 @@ class OracleLattice:
     ``[t][z][y][x][mu][row][col]`` (x fastest), complex128."""
 
     def __init__(self, N: int, Ns: int, Nt: int, beta: float, flux: int = 0,
-                 nhit: int = 10, lattice_id: int = 0, field_mode: int = FIELD_LINKS):
+                 nhit: int = 10, lattice_id: int = 0, field_mode: int = FIELD_LINKS,
+                 flux8: int = 0):
         self.N, self.Ns, self.Nt = N, Ns, Nt
         self.V = Ns ** 3 * Nt
         self.beta, self.flux, self.nhit, self.field_mode = beta, flux, nhit, field_mode
-        h = lib().oracle_create_ex(N, Ns, Nt, beta, flux, nhit, lattice_id, field_mode)
+        self.flux8 = flux8
+        h = lib().oracle_create_ex(N, Ns, Nt, beta, flux, flux8, nhit, lattice_id, field_mode)
         if not h:
             raise ValueError("oracle_create rejected the arguments")
         self._h = h

@@ -39,6 +39,10 @@
  *      phi(x) = 2 pi n x / Ns^2, applied on the right, Ut = U B; updates act on
  *      Ut and store U = Ut_new B^dagger (effective-link mode; a change of
  *      variables, so effective-link observables do not depend on n);
+ *   R10 lambda8 component (SU(3) only): with the generator sqrt(3) lambda8 =
+ *      diag(1, 1, -2), B_y(x) = diag(e^{i(p3 + p8)}, e^{i(-p3 + p8)},
+ *      e^{-2 i p8}), p3 = 2 pi n x / Ns^2, p8 = 2 pi n8 x / Ns^2, so every
+ *      diagonal phase is an integer multiple of 2 pi x / Ns^2;
  *   R9 frozen-boundary mode (the field imposed through fixed links, as in the
  *      background-field studies the paper cites): the spatial links of the
  *      time slice t = 0 hold B and are never updated or reunitarized, the
@@ -81,7 +85,7 @@ struct oracle_lattice {
     int N, Ns, Nt;
     long V;
     double beta;
-    int flux;
+    int flux, flux8;
     int field_mode;     /* ORACLE_FIELD_LINKS or ORACLE_FIELD_FROZEN */
     int nhit;
     uint32_t lattice_id;
@@ -311,12 +315,14 @@ static void put_link(oracle_lattice *L, long s, int mu, const mat *m)
 static mat background(const oracle_lattice *L, long s, int mu)
 {
     mat b = mat_identity(L->N);
-    if (mu == 1 && L->flux != 0) {
+    if (mu == 1 && (L->flux != 0 || L->flux8 != 0)) {
         int c[4];
         site_coords(L, s, c);
-        double phi = 2.0 * M_PI * L->flux * c[0] / ((double)L->Ns * L->Ns);
-        b.e[0][0] = cexp(I * phi);
-        b.e[1][1] = cexp(-I * phi);
+        double unit = 2.0 * M_PI * c[0] / ((double)L->Ns * L->Ns);
+        double p3 = unit * L->flux, p8 = unit * L->flux8;
+        b.e[0][0] = cexp(I * (p3 + p8));
+        b.e[1][1] = cexp(I * (-p3 + p8));
+        if (L->N == 3) b.e[2][2] = cexp(I * (-2.0 * p8));
     }
     return b;
 }
@@ -660,22 +666,24 @@ static mat reunitarize_one(int N, const mat *m)
 oracle_lattice *oracle_create(int N, int Ns, int Nt, double beta, int flux,
                               int nhit, uint32_t lattice_id)
 {
-    return oracle_create_ex(N, Ns, Nt, beta, flux, nhit, lattice_id,
+    return oracle_create_ex(N, Ns, Nt, beta, flux, 0, nhit, lattice_id,
                             ORACLE_FIELD_LINKS);
 }
 
 oracle_lattice *oracle_create_ex(int N, int Ns, int Nt, double beta, int flux,
-                                 int nhit, uint32_t lattice_id, int field_mode)
+                                 int flux8, int nhit, uint32_t lattice_id,
+                                 int field_mode)
 {
     if ((N != 2 && N != 3) || Ns < 2 || Nt < 2 || (Ns & 1) || (Nt & 1) ||
-        beta < 0.0 || nhit < 1 ||
+        beta < 0.0 || nhit < 1 || (N == 2 && flux8 != 0) ||
         (field_mode != ORACLE_FIELD_LINKS && field_mode != ORACLE_FIELD_FROZEN))
         return NULL;
     oracle_lattice *L = calloc(1, sizeof *L);
     if (!L) return NULL;
     L->N = N; L->Ns = Ns; L->Nt = Nt;
     L->V = (long)Ns * Ns * Ns * Nt;
-    L->beta = beta; L->flux = flux; L->nhit = nhit; L->field_mode = field_mode;
+    L->beta = beta; L->flux = flux; L->flux8 = flux8; L->nhit = nhit;
+    L->field_mode = field_mode;
     L->lattice_id = lattice_id;
     L->U = calloc((size_t)L->V * 4 * N * N, sizeof(cplx));
     if (!L->U) {

@@ -48,8 +48,10 @@ double oracle_uniform(uint32_t w);
  * allocation failure. */
 oracle_lattice *oracle_create(int N, int Ns, int Nt, double beta, int flux,
                               int nhit, uint32_t lattice_id);
+/* flux8: flux quanta of the lambda8 component (SU(3) only; 0 for SU(2)). */
 oracle_lattice *oracle_create_ex(int N, int Ns, int Nt, double beta, int flux,
-                                 int nhit, uint32_t lattice_id, int field_mode);
+                                 int flux8, int nhit, uint32_t lattice_id,
+                                 int field_mode);
 void oracle_destroy(oracle_lattice *L);
 void oracle_set_threads(int n);
 int oracle_get_threads(void);

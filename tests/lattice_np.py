@@ -25,23 +25,24 @@ def shift(Ns, Nt, s, mu, step):
     return index(Ns, c)
 
 
-def background(N, Ns, Nt, flux, s, mu):
-    """B_mu(x): lambda3 (sigma3) phase exp(i 2 pi n x / Ns^2) on y-links."""
+def background(N, Ns, Nt, flux, s, mu, flux8=0):
+    """B_mu(x) on y-links: exp(i p3 H3 + i p8 H8), H3 = diag(1, -1[, 0]),
+    H8 = diag(1, 1, -2) (sqrt(3) lambda8, SU(3) only), p = 2 pi n x / Ns^2."""
     b = np.eye(N, dtype=complex)
-    if mu == 1 and flux:
+    if mu == 1 and (flux or flux8):
         x = coords(Ns, Nt, s)[0]
-        phi = 2 * np.pi * flux * x / Ns ** 2
-        b[0, 0] = np.exp(1j * phi)
-        b[1, 1] = np.exp(-1j * phi)
+        unit = 2 * np.pi * x / Ns ** 2
+        h = np.array([1.0, -1.0, 0.0][:N]) * flux + (np.array([1.0, 1.0, -2.0]) * flux8 if N == 3 else 0.0)
+        b = np.diag(np.exp(1j * unit * h))
     return b
 
 
-def effective(U, Ns, Nt, flux):
+def effective(U, Ns, Nt, flux, flux8=0):
     N = U.shape[-1]
     out = U.copy()
-    if flux:
+    if flux or flux8:
         for s in range(U.shape[0]):
-            out[s, 1] = U[s, 1] @ background(N, Ns, Nt, flux, s, 1)
+            out[s, 1] = U[s, 1] @ background(N, Ns, Nt, flux, s, 1, flux8)
     return out
 
 

@@ -31,13 +31,16 @@ def test_cold_start_closed_form(oracle_mod, N):
     assert L.measure_bare() == [1.0, 1.0, 1.0]
 
 
-def flux_closed_form(N, Ns, n):
-    """Cold start, effective links = B: only xy-plaquettes see the field, with
-    phase difference 2 pi n / Ns^2 inside and -2 pi n (Ns-1)/Ns^2 across the
-    periodic x boundary."""
-    f = (lambda d: np.cos(d)) if N == 2 else (lambda d: (2 * np.cos(d) + 1) / 3)
-    inner = 2 * np.pi * n / Ns ** 2
-    edge = -2 * np.pi * n * (Ns - 1) / Ns ** 2
+def flux_closed_form(N, Ns, n, n8=0):
+    """Cold start, effective links = B: only xy-plaquettes see the field.  The
+    diagonal entry k of B_y carries the phase 2 pi h_k x / Ns^2 with
+    h = n (1, -1, 0) + n8 (1, 1, -2); an xy-plaquette is (1/N) sum_k cos of its
+    phase difference, 2 pi h_k / Ns^2 inside and -2 pi h_k (Ns-1)/Ns^2 across
+    the periodic x boundary."""
+    h = n * np.array([1.0, -1.0, 0.0][:N]) + (n8 * np.array([1.0, 1.0, -2.0]) if N == 3 else 0.0)
+    f = lambda d: np.cos(d * h).mean()
+    inner = 2 * np.pi / Ns ** 2
+    edge = -2 * np.pi * (Ns - 1) / Ns ** 2
     xy = ((Ns - 1) * f(inner) + f(edge)) / Ns
     ps = (xy + 2.0) / 3.0
     return (3 * ps + 3.0) / 6.0, ps, 1.0
