@@ -67,7 +67,8 @@ extern "C" {
 /* Field modes (sec. 1: lattice gauge theory in an external chromomagnetic
  * field; the paper gives no formula, so both are readings of that claim).
  * B_y(x) = diag(e^{i phi}, e^{-i phi} [, 1]), phi = 2 pi n x / Ns^2 along
- * lambda3 (sigma3 for SU(2)); B = 1 on x-, z- and t-links. */
+ * lambda3 (sigma3 for SU(2)), times the lambda8 part of qcd_lattice_create_ex
+ * for SU(3); B = 1 on x-, z- and t-links. */
 #define QCD_FIELD_LINKS 0  /* effective links U B on every link: updates and
                               measurements act on U B, U = (U B)_new B^+ is
                               stored (a change of variables of the n = 0
@@ -98,15 +99,22 @@ typedef struct qcd_lattice qcd_lattice;
 int qcd_lattice_create(qcd_lattice **out, int group, int Ns, int Nt,
                        double beta, int flux, int precision, int start,
                        uint64_t seed, void *stream);
-/* As qcd_lattice_create with an explicit field mode (QCD_FIELD_LINKS or
- * QCD_FIELD_FROZEN; anything else is QCD_ERR_INVALID_ARG).  In the frozen
- * mode the start is applied to every link and then the t = 0 spatial links are
- * overwritten with B; qcd_set_links stores what it is given, frozen links
- * included (a checkpoint holds them as B).  qcd_lattice_create is this call
- * with QCD_FIELD_LINKS. */
+/* As qcd_lattice_create with a lambda8 flux and an explicit field mode.
+ *   flux8       flux quanta of the lambda8 component (SU(3) only; nonzero for
+ *               group 2 is QCD_ERR_INVALID_ARG).  With the generator
+ *               sqrt(3) lambda8 = diag(1, 1, -2) the y-link background is
+ *               B_y(x) = diag(e^{i(p3 + p8)}, e^{i(-p3 + p8)}, e^{-2 i p8}),
+ *               p3 = 2 pi flux x / Ns^2, p8 = 2 pi flux8 x / Ns^2.
+ *   field_mode  QCD_FIELD_LINKS or QCD_FIELD_FROZEN (anything else is
+ *               QCD_ERR_INVALID_ARG).  In the frozen mode the start is applied
+ *               to every link and then the t = 0 spatial links are overwritten
+ *               with B; qcd_set_links stores what it is given, frozen links
+ *               included (a checkpoint holds them as B).
+ * qcd_lattice_create is this call with flux8 = 0 and QCD_FIELD_LINKS. */
 int qcd_lattice_create_ex(qcd_lattice **out, int group, int Ns, int Nt,
-                          double beta, int flux, int field_mode, int precision,
-                          int start, uint64_t seed, void *stream);
+                          double beta, int flux, int flux8, int field_mode,
+                          int precision, int start, uint64_t seed,
+                          void *stream);
 int qcd_lattice_destroy(qcd_lattice *lat);
 /* The field mode the lattice was created with. */
 int qcd_get_field_mode(qcd_lattice *lat, int *field_mode);

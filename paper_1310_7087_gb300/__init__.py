@@ -38,7 +38,7 @@ _vp, _i, _d, _u32, _u64, _sz = (ctypes.c_void_p, ctypes.c_int, ctypes.c_double,
 _P = ctypes.POINTER
 SIGNATURES = {
     "qcd_lattice_create": (_i, [_P(_vp), _i, _i, _i, _d, _i, _i, _i, _u64, _vp]),
-    "qcd_lattice_create_ex": (_i, [_P(_vp), _i, _i, _i, _d, _i, _i, _i, _i, _u64, _vp]),
+    "qcd_lattice_create_ex": (_i, [_P(_vp), _i, _i, _i, _d, _i, _i, _i, _i, _i, _u64, _vp]),
     "qcd_lattice_destroy": (_i, [_vp]),
     "qcd_get_field_mode": (_i, [_vp, _P(_i)]),
     "qcd_set_nhit": (_i, [_vp, _i]),
@@ -146,11 +146,11 @@ def qcd_lattice_create(group, Ns, Nt, beta, flux=0, precision=QCD_FP32_COMPRESSE
     return h
 
 
-def qcd_lattice_create_ex(group, Ns, Nt, beta, flux=0, field_mode=QCD_FIELD_LINKS,
+def qcd_lattice_create_ex(group, Ns, Nt, beta, flux=0, flux8=0, field_mode=QCD_FIELD_LINKS,
                           precision=QCD_FP32_COMPRESSED, start=QCD_HOT, seed=1,
                           stream=None) -> ctypes.c_void_p:
     h = ctypes.c_void_p()
-    _check(lib().qcd_lattice_create_ex(ctypes.byref(h), group, Ns, Nt, beta, flux, field_mode,
+    _check(lib().qcd_lattice_create_ex(ctypes.byref(h), group, Ns, Nt, beta, flux, flux8, field_mode,
                                        precision, start, seed, _stream_handle(stream)))
     return h
 
@@ -392,12 +392,12 @@ class Lattice:
     """Owning wrapper around one ``qcd_lattice`` handle."""
 
     def __init__(self, group, Ns, Nt, beta, flux=0, precision=QCD_FP32_COMPRESSED,
-                 start=QCD_HOT, seed=1, stream=None, nhit=10, field_mode=QCD_FIELD_LINKS):
+                 start=QCD_HOT, seed=1, stream=None, nhit=10, field_mode=QCD_FIELD_LINKS, flux8=0):
         self.group, self.Ns, self.Nt = group, Ns, Nt
         self.V = Ns ** 3 * Nt
         self.beta, self.flux, self.precision, self.seed = beta, flux, precision, seed
-        self.field_mode = field_mode
-        self.h = qcd_lattice_create_ex(group, Ns, Nt, beta, flux, field_mode, precision, start,
+        self.field_mode, self.flux8 = field_mode, flux8
+        self.h = qcd_lattice_create_ex(group, Ns, Nt, beta, flux, flux8, field_mode, precision, start,
                                        seed, stream)
         if nhit != 10:
             qcd_set_nhit(self.h, nhit)
@@ -456,15 +456,17 @@ class Lattice:
         """A lattice restored from a checkpoint written by ``save``."""
         import struct
         with open(path, "rb") as f:
-            head = f.read(72)
+            head = f.read(80)
         group, _, Ns, Nt, flux = struct.unpack_from("<IIIIi", head, 12)
         seed, beta = struct.unpack_from("<Qd", head, 48)
+        flux8 = struct.unpack_from("<i", head, 72)[0] if len(head) >= 76 else 0
         self = cls.__new__(cls)
         self.group, self.Ns, self.Nt = group, Ns, Nt
         self.V = Ns ** 3 * Nt
         self.beta, self.flux, self.precision, self.seed = beta, flux, precision, seed
         self.h = qcd_lattice_load(path, precision, stream)
         self.field_mode = qcd_get_field_mode(self.h)
+        self.flux8 = flux8
         return self
 
     @property

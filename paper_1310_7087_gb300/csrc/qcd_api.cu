@@ -93,7 +93,7 @@ void tune_store_locked() {
 
 struct qcd_lattice {
   const qcd::PolicyOps* ops = nullptr;
-  int group = 0, precision = 0, Ns = 0, Nt = 0, flux = 0, nhit = 10;
+  int group = 0, precision = 0, Ns = 0, Nt = 0, flux = 0, flux8 = 0, nhit = 10;
   int field_mode = QCD_FIELD_LINKS;
   double beta = 0.0;
   uint64_t seed = 0;
@@ -109,7 +109,7 @@ struct qcd_lattice {
   unsigned long long* d_exhausted = nullptr;
   double* d_meas = nullptr;
   double* d_partials = nullptr;
-  double2* d_phase64 = nullptr;
+  double2* d_phase64 = nullptr;  // 4 Ns entries: lambda3 phase, then the SU(3) diagonal
   float2* d_phase32 = nullptr;
   std::vector<SweepGraph> graphs;
   int profiling = 0;
@@ -120,14 +120,22 @@ struct qcd_lattice {
 
 namespace {
 
-__global__ void phase_table_kernel(double2* p64, float2* p32, int Ns, int flux) {
+__global__ void phase_table_kernel(double2* p64, float2* p32, int Ns, int flux, int flux8) {
   const int x = blockIdx.x * blockDim.x + threadIdx.x;
   if (x >= Ns) return;
   // phi = 2 pi n x / Ns^2, as sincospi of 2 n x / Ns^2 (exact argument reduction)
+  const double unit = 2.0 * double(x) / (double(Ns) * double(Ns));
   double s, c;
-  sincospi(2.0 * double(flux) * double(x) / (double(Ns) * double(Ns)), &s, &c);
+  sincospi(double(flux) * unit, &s, &c);
   p64[x] = make_double2(c, s);
   p32[x] = make_float2(float(c), float(s));
+  // SU(3) diagonal: theta = 2 pi x / Ns^2 (n + n8, -n + n8, -2 n8)
+  const int h[3] = {flux + flux8, -flux + flux8, -2 * flux8};
+  for (int k = 0; k < 3; ++k) {
+    sincospi(double(h[k]) * unit, &s, &c);
+    p64[Ns + 3 * x + k] = make_double2(c, s);
+    p32[Ns + 3 * x + k] = make_float2(float(c), float(s));
+  }
 }
 
 const qcd::PolicyOps* pick_ops(int group, int precision) {
@@ -149,6 +157,7 @@ qcd::Ctx make_ctx(const qcd_lattice* L, uint64_t seed) {
   a.field_mode = L->field_mode;
   a.phase64 = L->d_phase64;
   a.phase32 = L->d_phase32;
+  a.flux8 = L->flux8;
   a.exhausted = L->d_exhausted;
   a.partials = L->d_partials;
   a.meas_out = L->d_meas;
@@ -277,7 +286,7 @@ std::string tune_key(const qcd_lattice* L) {
   }
   char buf[256];
   snprintf(buf, sizeof buf, "su%d_p%d_%dx%d_f%d_%s", L->group, L->precision, L->Ns, L->Nt,
-           L->flux != 0 && L->field_mode == QCD_FIELD_LINKS ? 1 : 0,
+           L->field_mode != QCD_FIELD_LINKS ? 0 : L->flux8 != 0 ? 2 : L->flux != 0 ? 1 : 0,
            dev.c_str());
   return buf;
 }
@@ -366,13 +375,14 @@ const char* qcd_last_error(void) { return g_last_error.c_str(); }
 
 int qcd_lattice_create(qcd_lattice** out, int group, int Ns, int Nt, double beta, int flux, int precision,
                        int start, uint64_t seed, void* stream) {
-  return qcd_lattice_create_ex(out, group, Ns, Nt, beta, flux, QCD_FIELD_LINKS, precision, start, seed, stream);
+  return qcd_lattice_create_ex(out, group, Ns, Nt, beta, flux, 0, QCD_FIELD_LINKS, precision, start, seed, stream);
 }
 
-int qcd_lattice_create_ex(qcd_lattice** out, int group, int Ns, int Nt, double beta, int flux, int field_mode,
-                          int precision, int start, uint64_t seed, void* stream) {
+int qcd_lattice_create_ex(qcd_lattice** out, int group, int Ns, int Nt, double beta, int flux, int flux8,
+                          int field_mode, int precision, int start, uint64_t seed, void* stream) {
   if (!out) return set_error(QCD_ERR_INVALID_ARG, "out is null");
   *out = nullptr;
+  if (group == 2 && flux8 != 0) return set_error(QCD_ERR_INVALID_ARG, "the lambda8 flux needs SU(3)");
   if (field_mode != QCD_FIELD_LINKS && field_mode != QCD_FIELD_FROZEN)
     return set_error(QCD_ERR_INVALID_ARG, "unknown field mode %d", field_mode);
   if (group != 2 && group != 3) return set_error(QCD_ERR_INVALID_ARG, "group must be 2 or 3, got %d", group);
@@ -393,6 +403,7 @@ int qcd_lattice_create_ex(qcd_lattice** out, int group, int Ns, int Nt, double b
   L->Ns = Ns;
   L->Nt = Nt;
   L->flux = flux;
+  L->flux8 = flux8;
   L->field_mode = field_mode;
   L->beta = beta;
   L->seed = seed;
@@ -413,8 +424,8 @@ int qcd_lattice_create_ex(qcd_lattice** out, int group, int Ns, int Nt, double b
   if (cudaMalloc(&L->links, L->link_bytes) != cudaSuccess ||
       cudaMalloc(reinterpret_cast<void**>(&L->d_small), small_bytes) != cudaSuccess ||
       cudaMalloc(reinterpret_cast<void**>(&L->d_partials), n_part * sizeof(double)) != cudaSuccess ||
-      cudaMalloc(reinterpret_cast<void**>(&L->d_phase64), Ns * sizeof(double2)) != cudaSuccess ||
-      cudaMalloc(reinterpret_cast<void**>(&L->d_phase32), Ns * sizeof(float2)) != cudaSuccess) {
+      cudaMalloc(reinterpret_cast<void**>(&L->d_phase64), 4 * Ns * sizeof(double2)) != cudaSuccess ||
+      cudaMalloc(reinterpret_cast<void**>(&L->d_phase32), 4 * Ns * sizeof(float2)) != cudaSuccess) {
     cudaGetLastError();
     return fail(set_error(QCD_ERR_OOM, "device allocation of %zu bytes of links failed", L->link_bytes));
   }
@@ -423,7 +434,7 @@ int qcd_lattice_create_ex(qcd_lattice** out, int group, int Ns, int Nt, double b
   L->d_meas = reinterpret_cast<double*>(L->d_small + 64);
   if ((e = cudaMemsetAsync(L->d_small, 0, small_bytes, L->stream)) != cudaSuccess)
     return fail(set_error(QCD_ERR_CUDA, "memset: %s", cudaGetErrorString(e)));
-  phase_table_kernel<<<(Ns + 63) / 64, 64, 0, L->stream>>>(L->d_phase64, L->d_phase32, Ns, flux);
+  phase_table_kernel<<<(Ns + 63) / 64, 64, 0, L->stream>>>(L->d_phase64, L->d_phase32, Ns, flux, flux8);
   if ((e = cudaGetLastError()) != cudaSuccess)
     return fail(set_error(QCD_ERR_CUDA, "phase table: %s", cudaGetErrorString(e)));
   if ((e = L->ops->start(make_ctx(L, seed), start, L->stream)) != cudaSuccess)
@@ -702,8 +713,10 @@ int qcd_save(qcd_lattice* L, const char* path) {
   if (int rc = qcd_get_links(L, buf.data())) return rc;
   FILE* f = fopen(path, "wb");
   if (!f) return set_error(QCD_ERR_INVALID_ARG, "cannot open %s for writing", path);
-  const uint64_t pad8 = 0;
-  const bool ok = fwrite(&h, sizeof h, 1, f) == 1 && fwrite(&pad8, 8, 1, f) == 1 &&
+  // the 8 bytes after the header: lambda8 flux (int32; 0 in files written
+  // before it existed) and 4 reserved zero bytes
+  const int32_t tail[2] = {int32_t(L->flux8), 0};
+  const bool ok = fwrite(&h, sizeof h, 1, f) == 1 && fwrite(tail, 8, 1, f) == 1 &&
                   fwrite(buf.data(), sizeof(double), n, f) == n;
   if (fclose(f) != 0 || !ok) return set_error(QCD_ERR_INVALID_ARG, "writing %s failed", path);
   return QCD_OK;
@@ -715,14 +728,15 @@ int qcd_lattice_load(qcd_lattice** out, const char* path, int precision, void* s
   FILE* f = fopen(path, "rb");
   if (!f) return set_error(QCD_ERR_INVALID_ARG, "cannot open %s", path);
   CheckpointHeader h{};
-  uint64_t pad8 = 0;
-  if (fread(&h, sizeof h, 1, f) != 1 || fread(&pad8, 8, 1, f) != 1 || std::memcmp(h.magic, kMagic, 8) != 0 ||
+  int32_t tail[2] = {0, 0};
+  if (fread(&h, sizeof h, 1, f) != 1 || fread(tail, 8, 1, f) != 1 || std::memcmp(h.magic, kMagic, 8) != 0 ||
       h.version != 1 || (h.group != 2 && h.group != 3) || h.field_mode > 1 || h.Ns < 2 || h.Nt < 2 || h.Ns > 1290 || h.Nt > (1u << 30)) {
     fclose(f);
     return set_error(QCD_ERR_INVALID_ARG, "%s is not a version-1 checkpoint", path);
   }
   qcd_lattice* L = nullptr;
-  int rc = qcd_lattice_create_ex(&L, int(h.group), int(h.Ns), int(h.Nt), h.beta, h.flux, int(h.field_mode),
+  int rc = qcd_lattice_create_ex(&L, int(h.group), int(h.Ns), int(h.Nt), h.beta, h.flux, int(tail[0]),
+                                 int(h.field_mode),
                                  precision, QCD_COLD, h.seed, stream);
   if (rc) {
     fclose(f);

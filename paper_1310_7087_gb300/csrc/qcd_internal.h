@@ -26,12 +26,20 @@ struct Ctx {
   int flux;                     // 0: no background field
   int field_mode;               // 0: phase on every y-link (effective links U B);
                                 // 1: field on the frozen spatial links of t = 0
-  const double2* phase64;       // per x: (cos phi, sin phi), phi = 2 pi n x / Ns^2
+  int flux8;                    // lambda8 flux quanta (SU(3)); 0: lambda3 only
+  // Background tables, 4 Ns entries each: [x] = (cos phi, sin phi) with
+  // phi = 2 pi n x / Ns^2, then [Ns + 3x + k] = e^{i theta_k(x)}, the diagonal
+  // of the SU(3) y-link background diag(e^{i(p3+p8)}, e^{i(-p3+p8)}, e^{-2i p8}).
+  // (The argument struct is kept at 120 bytes: growing it past 128 bytes
+  // measurably slowed every kernel that takes it.)
+  const double2* phase64;
   const float2* phase32;
   unsigned long long* exhausted;
   double* partials;             // measurement scratch, measure_partials() doubles
   double* meas_out;             // 5 doubles: P, P_s, P_t, Re L, Im L
 };
+
+static_assert(sizeof(Ctx) <= 128, "kernel argument struct grew past 128 bytes");
 
 constexpr int MEAS_THREADS = 256;
 constexpr int FINAL_THREADS = 1024;
@@ -63,7 +71,10 @@ struct PolicyOps {
 };
 
 // Effective-link phases are applied only in field mode 0 with a field.
-inline bool phases_on_links(const Ctx& a) { return a.flux != 0 && a.field_mode == 0; }
+inline bool phases_on_links(const Ctx& a) { return (a.flux != 0 || a.flux8 != 0) && a.field_mode == 0; }
+// Which background multiply the SU(3) FP32 phase kernel instantiates:
+// 0 none, 1 lambda3 only (columns 0, 1), 2 general diagonal (all columns).
+inline int su3_field_level(const Ctx& a) { return !phases_on_links(a) ? 0 : (a.flux8 != 0 ? 2 : 1); }
 
 // Record the message returned by qcd_last_error() on this thread; returns code.
 int set_last_error(int code, const char* msg);

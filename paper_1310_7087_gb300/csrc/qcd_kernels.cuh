@@ -187,15 +187,52 @@ __device__ __forceinline__ void load_phase<double>(const Ctx& a, int x, double& 
   s = v.y;
 }
 
+// The diagonal of the SU(3) y-link background at x: b[k] = e^{i theta_k(x)}.
+template <typename R>
+__device__ __forceinline__ void load_bdiag(const Ctx& a, int x, Cx<R> b[3]);
+template <>
+__device__ __forceinline__ void load_bdiag<float>(const Ctx& a, int x, Cx<float> b[3]) {
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    const float2 v = __ldg(a.phase32 + a.g.Ns + 3 * x + k);
+    b[k] = {v.x, v.y};
+  }
+}
+template <>
+__device__ __forceinline__ void load_bdiag<double>(const Ctx& a, int x, Cx<double> b[3]) {
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    const double2 v = __ldg(a.phase64 + a.g.Ns + 3 * x + k);
+    b[k] = {v.x, v.y};
+  }
+}
+
+// u B for B = diag(b_0, b_1, b_2): column k times b_k.
+template <typename R>
+__device__ __forceinline__ M3<R> right_bdiag(M3<R> u, const Cx<R> b[3]) {
+#pragma unroll
+  for (int r = 0; r < 3; ++r)
+#pragma unroll
+    for (int k = 0; k < 3; ++k) u.e[r][k] = u.e[r][k] * b[k];
+  return u;
+}
+
 // Effective link Ut_mu(site) = U_mu(site) B_mu(site).
-template <class P, bool FIELD, bool CG = false>
+template <class P, int FIELD, bool CG = false>
 __device__ __forceinline__ typename P::Link load_eff(const Ctx& a, int mu, const Site& c) {
   using R = typename P::Real;
   typename P::Link u = P::template load<CG>(a.links, a.g, mu, parity_of(c), lex(a.g, c) >> 1);
-  if (FIELD && mu == 1) {
+  if (FIELD == 1 && mu == 1) {  // lambda3 (sigma3): columns 0 and 1
     R ph_c, ph_s;
     load_phase<R>(a, c.x, ph_c, ph_s);
     u = Alg<R>::right_phase(u, ph_c, ph_s);
+  }
+  if constexpr (P::N == 3 && FIELD == 2) {  // lambda3 + lambda8: every column
+    if (mu == 1) {
+      Cx<R> b[3];
+      load_bdiag<R>(a, c.x, b);
+      u = right_bdiag(u, b);
+    }
   }
   return u;
 }
@@ -203,7 +240,7 @@ __device__ __forceinline__ typename P::Link load_eff(const Ctx& a, int mu, const
 // Staple sum of U_mu(x) on effective links:
 //   A = sum_{nu != mu} Ut_nu(x+mu) Ut_mu(x+nu)^+ Ut_nu(x)^+
 //                    + (Ut_mu(x-nu) Ut_nu(x+mu-nu))^+ Ut_nu(x-nu)
-template <class P, bool FIELD, bool CG = false>
+template <class P, int FIELD, bool CG = false>
 __device__ __forceinline__ typename P::Link staple(const Ctx& a, const Site& x, int mu) {
   using R = typename P::Real;
   using A = Alg<R>;
@@ -265,7 +302,7 @@ __device__ __forceinline__ bool frozen_link(const Ctx& a, int mu, int t) {
   return a.field_mode == 1 && mu < 3 && t == 0;
 }
 
-template <typename R, bool FIELD, int KIND>
+template <typename R, int FIELD, int KIND>
 __global__ void __maxnreg__(QCD_SU3_PHASE_MAXNREG) su3_phase_kernel(const Ctx a, int parity, int mu) {
   using P = SU3Policy<R>;
   const int h = blockIdx.x * blockDim.x + threadIdx.x;
@@ -275,10 +312,14 @@ __global__ void __maxnreg__(QCD_SU3_PHASE_MAXNREG) su3_phase_kernel(const Ctx a,
   const M3<R> A = staple<P, FIELD>(a, x, mu);
   M3<R> U = P::load(a.links, a.g, mu, parity, h);
   M3<R> Ut = U;
-  if (FIELD && mu == 1) {
+  if (FIELD == 1 && mu == 1) {
     R bc, bs;
     load_phase<R>(a, x.x, bc, bs);
     Ut = Alg<R>::right_phase(U, bc, bs);
+  } else if (FIELD == 2 && mu == 1) {
+    Cx<R> b[3];
+    load_bdiag<R>(a, x.x, b);
+    Ut = right_bdiag(U, b);
   }
   M3<R> W = m3_mul(Ut, A);
   const uint32_t s = uint32_t(lex(a.g, x));
@@ -609,7 +650,8 @@ __global__ void start_kernel(const Ctx a, int hot) {
 }
 
 // Frozen-boundary mode: the spatial links of the t = 0 slice hold B (y-links
-// diag(e^{i phi}, e^{-i phi} [,1]), x- and z-links unity).
+// diag(e^{i phi}, e^{-i phi}) for SU(2), the lambda3 + lambda8 diagonal for
+// SU(3); x- and z-links unity).
 template <class P>
 __global__ void set_frozen_kernel(const Ctx a) {
   using R = typename P::Real;
@@ -618,20 +660,22 @@ __global__ void set_frozen_kernel(const Ctx a) {
   if (idx >= 3 * V3) return;
   const int mu = int(idx / V3), s = int(idx % V3);  // t = 0: s is the spatial index
   const Site x{s % a.g.Ns, (s / a.g.Ns) % a.g.Ns, s / (a.g.Ns * a.g.Ns), 0};
-  double c = 1.0, sn = 0.0;
-  if (mu == 1) {
-    const double2 ph = a.phase64[x.x];
-    c = ph.x;
-    sn = ph.y;
-  }
   typename P::Link u;
   if constexpr (P::N == 2) {
+    double c = 1.0, sn = 0.0;
+    if (mu == 1) {
+      const double2 ph = a.phase64[x.x];
+      c = ph.x;
+      sn = ph.y;
+    }
     u = {R(c), R(0), R(0), R(sn)};
   } else {
     m3_zero(u);
-    u.e[0][0] = {R(c), R(sn)};
-    u.e[1][1] = {R(c), R(-sn)};
-    u.e[2][2] = {R(1), R(0)};
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      const double2 b = mu == 1 ? a.phase64[a.g.Ns + 3 * x.x + k] : make_double2(1.0, 0.0);
+      u.e[k][k] = {R(b.x), R(b.y)};
+    }
   }
   P::store(a.links, a.g, mu, parity_of(x), lex(a.g, x) >> 1, u);
 }
@@ -668,7 +712,7 @@ __device__ __forceinline__ void block_sum2(double& v0, double& v1, double* parti
 
 // Plaquettes of one site (index idx over both parities): spatial sum into v0,
 // temporal sum into v1, (1/N) Re Tr each, FP64.
-template <class P, bool FIELD, bool CG = false>
+template <class P, int FIELD, bool CG = false>
 __device__ __forceinline__ void plaquette_site(const Ctx& a, int64_t idx, double& v0, double& v1) {
   using R = typename P::Real;
   using A = Alg<R>;
@@ -713,8 +757,8 @@ __device__ __forceinline__ void polyakov_site(const Ctx& a, int64_t idx, double&
   }
 }
 
-template <class P, bool FIELD>
-__global__ void __launch_bounds__(MEAS_THREADS) measure_kernel(const Ctx a, int n_plaq_blocks) {
+template <class P, int FIELD>
+__global__ void __launch_bounds__(MEAS_THREADS, 2) measure_kernel(const Ctx a, int n_plaq_blocks) {
   double v0 = 0.0, v1 = 0.0;
   if (int(blockIdx.x) < n_plaq_blocks) {
     const int64_t idx = int64_t(blockIdx.x) * MEAS_THREADS + threadIdx.x;
@@ -830,22 +874,25 @@ __global__ void from_canonical_kernel(const Ctx a, const double* in) {
 // ---------------------------------------------------------------------------
 inline unsigned grid_for(int64_t n, int block) { return unsigned((n + block - 1) / block); }
 
-template <class P, bool FIELD, int KIND>
+template <class P, int FIELD, int KIND>
 inline void launch_phase_t(const Ctx& a, int parity, int mu, int block, cudaStream_t st) {
   static_assert(P::N == 3, "SU(2) uses the kernels of qcd_su2c.cuh");
   su3_phase_kernel<typename P::Real, FIELD, KIND><<<grid_for(a.g.Vh, block), block, 0, st>>>(a, parity, mu);
 }
 
+template <class P, int KIND>
+inline void launch_phase_level(const Ctx& a, int parity, int mu, int block, cudaStream_t st) {
+  switch (su3_field_level(a)) {
+    case 0: launch_phase_t<P, 0, KIND>(a, parity, mu, block, st); break;
+    case 1: launch_phase_t<P, 1, KIND>(a, parity, mu, block, st); break;
+    default: launch_phase_t<P, 2, KIND>(a, parity, mu, block, st); break;
+  }
+}
+
 template <class P>
 cudaError_t launch_phase(const Ctx& a, int kind, int parity, int mu, int block, cudaStream_t st) {
-  const bool field = phases_on_links(a);
-  if (kind == KIND_HB) {
-    if (field) launch_phase_t<P, true, KIND_HB>(a, parity, mu, block, st);
-    else launch_phase_t<P, false, KIND_HB>(a, parity, mu, block, st);
-  } else {
-    if (field) launch_phase_t<P, true, KIND_OR>(a, parity, mu, block, st);
-    else launch_phase_t<P, false, KIND_OR>(a, parity, mu, block, st);
-  }
+  if (kind == KIND_HB) launch_phase_level<P, KIND_HB>(a, parity, mu, block, st);
+  else launch_phase_level<P, KIND_OR>(a, parity, mu, block, st);
   return cudaGetLastError();
 }
 
@@ -876,10 +923,16 @@ cudaError_t launch_set_frozen(const Ctx& a, cudaStream_t st) {
 template <class P>
 cudaError_t launch_measure(const Ctx& a, int effective, cudaStream_t st) {
   const int np = meas_plaq_blocks(a.g), nl = meas_poly_blocks(a.g);
-  if (effective && phases_on_links(a))
-    measure_kernel<P, true><<<np + nl, MEAS_THREADS, 0, st>>>(a, np);
-  else
-    measure_kernel<P, false><<<np + nl, MEAS_THREADS, 0, st>>>(a, np);
+  if constexpr (P::N == 2) {
+    if (effective && phases_on_links(a)) measure_kernel<P, 1><<<np + nl, MEAS_THREADS, 0, st>>>(a, np);
+    else measure_kernel<P, 0><<<np + nl, MEAS_THREADS, 0, st>>>(a, np);
+  } else {
+    switch (effective ? su3_field_level(a) : 0) {
+      case 0: measure_kernel<P, 0><<<np + nl, MEAS_THREADS, 0, st>>>(a, np); break;
+      case 1: measure_kernel<P, 1><<<np + nl, MEAS_THREADS, 0, st>>>(a, np); break;
+      default: measure_kernel<P, 2><<<np + nl, MEAS_THREADS, 0, st>>>(a, np); break;
+    }
+  }
   measure_final_kernel<<<1, FINAL_THREADS, 0, st>>>(a, np, nl);
   return cudaGetLastError();
 }
@@ -896,7 +949,7 @@ cudaError_t launch_from_canonical(const Ctx& a, const double* in, cudaStream_t s
   return cudaGetLastError();
 }
 
-template <class P, bool FIELD, int KIND>
+template <class P, int FIELD, int KIND>
 int phase_block_limit() {
   cudaFuncAttributes attr{};
   const cudaError_t e = cudaFuncGetAttributes(&attr, su3_phase_kernel<typename P::Real, FIELD, KIND>);
@@ -905,10 +958,12 @@ int phase_block_limit() {
 
 template <class P>
 int max_phase_block() {
-  int m = phase_block_limit<P, false, KIND_HB>();
-  m = std::min(m, phase_block_limit<P, true, KIND_HB>());
-  m = std::min(m, phase_block_limit<P, false, KIND_OR>());
-  m = std::min(m, phase_block_limit<P, true, KIND_OR>());
+  int m = phase_block_limit<P, 0, KIND_HB>();
+  m = std::min(m, phase_block_limit<P, 1, KIND_HB>());
+  m = std::min(m, phase_block_limit<P, 2, KIND_HB>());
+  m = std::min(m, phase_block_limit<P, 0, KIND_OR>());
+  m = std::min(m, phase_block_limit<P, 1, KIND_OR>());
+  m = std::min(m, phase_block_limit<P, 2, KIND_OR>());
   return m;
 }
 

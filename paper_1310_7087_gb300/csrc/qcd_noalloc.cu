@@ -30,9 +30,10 @@ int noalloc_error(int code, const std::string& msg) { return qcd::set_last_error
 
 // Layout inside the scratch array (byte offsets).
 constexpr size_t kMeasOff = 0;      // 5 doubles
-constexpr size_t kPhaseOff = 64;    // Ns double2, then Ns float2
-size_t partials_offset(int Ns) { return (kPhaseOff + size_t(Ns) * 24 + 255) / 256 * 256; }
+constexpr size_t kPhaseOff = 64;    // 4 Ns double2, then 4 Ns float2
+size_t partials_offset(int Ns) { return (kPhaseOff + size_t(Ns) * 96 + 255) / 256 * 256; }
 
+// The lambda3 phase per x and the SU(3) diagonal of B_y (no lambda8 part).
 __global__ void noalloc_phase_table(double2* p64, float2* p32, int Ns, int flux) {
   const int x = blockIdx.x * blockDim.x + threadIdx.x;
   if (x >= Ns) return;
@@ -40,6 +41,11 @@ __global__ void noalloc_phase_table(double2* p64, float2* p32, int Ns, int flux)
   sincospi(2.0 * double(flux) * double(x) / (double(Ns) * double(Ns)), &s, &c);
   p64[x] = make_double2(c, s);
   p32[x] = make_float2(float(c), float(s));
+  const double2 d[3] = {make_double2(c, s), make_double2(c, -s), make_double2(1.0, 0.0)};
+  for (int k = 0; k < 3; ++k) {
+    p64[Ns + 3 * x + k] = d[k];
+    p32[Ns + 3 * x + k] = make_float2(float(d[k].x), float(d[k].y));
+  }
 }
 
 // Device address of the scratch array on the current device; looked up once
@@ -100,7 +106,7 @@ extern "C" int qcd_measure_noalloc(const void* links, int group, int precision, 
   a.g = g;
   a.flux = flux;
   a.phase64 = reinterpret_cast<double2*>(base + kPhaseOff);
-  a.phase32 = reinterpret_cast<float2*>(base + kPhaseOff + size_t(Ns) * 16);
+  a.phase32 = reinterpret_cast<float2*>(base + kPhaseOff + size_t(Ns) * 64);
   a.partials = reinterpret_cast<double*>(base + partials_offset(Ns));
   a.meas_out = reinterpret_cast<double*>(base + kMeasOff);
 

@@ -207,18 +207,25 @@ __device__ __forceinline__ void su3c_left_rotate(M3<float>& m, const Quat<float>
 }
 
 // Effective link of direction D at site x, whose parity PAR is known.
-template <bool FIELD, int D>
+template <int FIELD, int D>
 __device__ __forceinline__ Rows2 su3c_eff(const Ctx& a, int par, const LexSite& x) {
   Rows2 r = su3c_load(a.links, a.g, D, par, x.s >> 1);
-  if (FIELD && D == 1) {
+  if (FIELD == 1 && D == 1) {
     const float2 ph = __ldg(a.phase32 + x.c[0]);
     su3c_phase(r, ph.x, ph.y);
+  } else if (FIELD == 2 && D == 1) {
+    Cx<float> b[3];
+    load_bdiag<float>(a, x.c[0], b);
+#pragma unroll
+    for (int i = 0; i < 2; ++i)
+#pragma unroll
+      for (int k = 0; k < 3; ++k) r.e[i][k] = xy_mul(xy_first(r.e[i][k], b[k]));
   }
   return r;
 }
 
 // Staple sum of U_MU(x) (x of parity p) on effective links, full 3x3.
-template <bool FIELD, int MU>
+template <int FIELD, int MU>
 __device__ __forceinline__ M3<float> su3c_staple(const Ctx& a, int p, const LexSite& x) {
   M3<float> A;
   m3_zero(A);
@@ -254,11 +261,18 @@ __device__ __forceinline__ M3<float> su3c_staple(const Ctx& a, int p, const LexS
 }
 
 // Heat-bath or overrelaxation of U_MU(x) given its staple sum A.
-template <bool FIELD, int KIND, int MU>
+template <int FIELD, int KIND, int MU>
 __device__ __forceinline__ void su3c_update(const Ctx& a, int parity, int h, const LexSite& x, const M3<float>& A,
                                             M3<float> U) {
   M3<float> Ut = U;
-  if (FIELD && MU == 1) {
+  if (FIELD == 2 && MU == 1) {
+    Cx<float> b[3];
+    load_bdiag<float>(a, x.c[0], b);
+#pragma unroll
+    for (int r = 0; r < 3; ++r)
+#pragma unroll
+      for (int k = 0; k < 3; ++k) Ut.e[r][k] = xy_mul(xy_first(U.e[r][k], b[k]));
+  } else if (FIELD == 1 && MU == 1) {
     const float2 ph = __ldg(a.phase32 + x.c[0]);
     const Cx<float> p{ph.x, ph.y}, pc{ph.x, -ph.y};
 #pragma unroll
@@ -306,7 +320,7 @@ __device__ __forceinline__ void su3c_update(const Ctx& a, int parity, int h, con
   SU3Policy<float>::store(a.links, a.g, MU, parity, h, U);
 }
 
-template <bool FIELD, int KIND, int MU>
+template <int FIELD, int KIND, int MU>
 __global__ void __maxnreg__(QCD_SU3_PHASE_MAXNREG) su3c_phase_kernel(const Ctx a, int parity) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= a.g.Vh) return;
@@ -317,13 +331,13 @@ __global__ void __maxnreg__(QCD_SU3_PHASE_MAXNREG) su3c_phase_kernel(const Ctx a
   su3c_update<FIELD, KIND, MU>(a, parity, h, x, A, su3c_full(su3c_load(a.links, a.g, MU, parity, h)));
 }
 
-template <bool FIELD, int KIND, int MU>
+template <int FIELD, int KIND, int MU>
 inline void su3c_launch_one(const Ctx& a, int parity, int block, cudaStream_t st) {
   const unsigned grid = grid_for(a.g.Vh, block);
   su3c_phase_kernel<FIELD, KIND, MU><<<grid, block, 0, st>>>(a, parity);
 }
 
-template <bool FIELD, int KIND>
+template <int FIELD, int KIND>
 inline void su3c_launch_kind(const Ctx& a, int parity, int mu, int block, cudaStream_t st) {
   switch (mu) {
     case 0: su3c_launch_one<FIELD, KIND, 0>(a, parity, block, st); break;
@@ -333,34 +347,38 @@ inline void su3c_launch_kind(const Ctx& a, int parity, int mu, int block, cudaSt
   }
 }
 
-inline cudaError_t su3c_launch_phase(const Ctx& a, int kind, int parity, int mu, int block, cudaStream_t st) {
-  const bool field = phases_on_links(a);
-  if (kind == KIND_HB) {
-    if (field) su3c_launch_kind<true, KIND_HB>(a, parity, mu, block, st);
-    else su3c_launch_kind<false, KIND_HB>(a, parity, mu, block, st);
-  } else {
-    if (field) su3c_launch_kind<true, KIND_OR>(a, parity, mu, block, st);
-    else su3c_launch_kind<false, KIND_OR>(a, parity, mu, block, st);
+template <int KIND>
+inline void su3c_launch_level(const Ctx& a, int parity, int mu, int block, cudaStream_t st) {
+  switch (su3_field_level(a)) {
+    case 0: su3c_launch_kind<0, KIND>(a, parity, mu, block, st); break;
+    case 1: su3c_launch_kind<1, KIND>(a, parity, mu, block, st); break;
+    default: su3c_launch_kind<2, KIND>(a, parity, mu, block, st); break;
   }
+}
+
+inline cudaError_t su3c_launch_phase(const Ctx& a, int kind, int parity, int mu, int block, cudaStream_t st) {
+  if (kind == KIND_HB) su3c_launch_level<KIND_HB>(a, parity, mu, block, st);
+  else su3c_launch_level<KIND_OR>(a, parity, mu, block, st);
   return cudaGetLastError();
 }
 
-template <bool FIELD, int KIND, int MU>
+template <int FIELD, int KIND, int MU>
 int su3c_block_limit() {
   cudaFuncAttributes attr{};
   return cudaFuncGetAttributes(&attr, su3c_phase_kernel<FIELD, KIND, MU>) == cudaSuccess ? attr.maxThreadsPerBlock
                                                                                         : 0;
 }
 
-template <bool FIELD, int KIND>
+template <int FIELD, int KIND>
 int su3c_block_limit_mu() {
   return std::min(std::min(su3c_block_limit<FIELD, KIND, 0>(), su3c_block_limit<FIELD, KIND, 1>()),
                   std::min(su3c_block_limit<FIELD, KIND, 2>(), su3c_block_limit<FIELD, KIND, 3>()));
 }
 
 inline int su3c_max_phase_block() {
-  return std::min(std::min(su3c_block_limit_mu<false, KIND_HB>(), su3c_block_limit_mu<true, KIND_HB>()),
-                  std::min(su3c_block_limit_mu<false, KIND_OR>(), su3c_block_limit_mu<true, KIND_OR>()));
+  int m = std::min(std::min(su3c_block_limit_mu<0, KIND_HB>(), su3c_block_limit_mu<1, KIND_HB>()),
+                   std::min(su3c_block_limit_mu<0, KIND_OR>(), su3c_block_limit_mu<1, KIND_OR>()));
+  return std::min(m, std::min(su3c_block_limit_mu<2, KIND_HB>(), su3c_block_limit_mu<2, KIND_OR>()));
 }
 
 }  // namespace qcd
