@@ -148,6 +148,13 @@ int qcd_reunitarize(qcd_lattice *lat);
 int qcd_measure(qcd_lattice *lat, double *plaquette, double *polyakov);
 /* The same plaquettes on the bare links U (they depend on the field). */
 int qcd_measure_bare(qcd_lattice *lat, double *plaquette);
+/* qcd_measure without the wait: enqueues the measurement and the copy of the
+ * five results {P, P_s, P_t, Re L, Im L} into host_out (host double[5];
+ * page-locked memory lets the copy overlap other work) on the lattice's
+ * stream and returns.  host_out must stay valid, and is filled, once the
+ * stream has been synchronized.  Not counted by the live profile.  For
+ * pipelines that keep several lattices in flight on separate streams. */
+int qcd_measure_async(qcd_lattice *lat, double *host_out);
 
 /* Links in the canonical FP64 host layout (4 V N^2 complex numbers).
  * set_links rounds to the storage (FP32-12 keeps rows 1-2; SU(2) keeps the
@@ -227,7 +234,7 @@ int qcd_get_profile(qcd_lattice *lat, double *ms, unsigned long long *launches);
  * Scratch: one file-scope device array of QCD_NOALLOC_SCRATCH_BYTES (512 KiB)
  * per GPU that loads the library, held until the process exits.  A lattice
  * needs 16 (ceil(V/256) + ceil(Ns^3/256)) bytes of block partials plus
- * at most 24 Ns + 320 bytes; every lattice of at most 4,194,304 sites (such as
+ * at most 96 Ns + 320 bytes; every lattice of at most 4,194,304 sites (such as
  * 64^3 x 16) fits, a lattice that needs more returns QCD_ERR_INVALID_ARG with
  * the sizes in qcd_last_error().  The
  * first call on a device looks up the array's device address (with that device

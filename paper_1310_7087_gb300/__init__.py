@@ -46,6 +46,7 @@ SIGNATURES = {
     "qcd_phase": (_i, [_vp, _i, _i, _i, _u64]),
     "qcd_reunitarize": (_i, [_vp]),
     "qcd_measure": (_i, [_vp, _P(_d), _P(_d)]),
+    "qcd_measure_async": (_i, [_vp, _vp]),
     "qcd_measure_bare": (_i, [_vp, _P(_d)]),
     "qcd_get_links": (_i, [_vp, _P(_d)]),
     "qcd_set_links": (_i, [_vp, _P(_d)]),
@@ -159,6 +160,12 @@ def qcd_get_field_mode(h) -> int:
     v = ctypes.c_int()
     _check(lib().qcd_get_field_mode(h, ctypes.byref(v)))
     return v.value
+
+
+def qcd_measure_async(h, host_out_ptr: int) -> None:
+    """Enqueue the measurement; the five doubles land at host_out_ptr once the
+    lattice's stream is synchronized."""
+    _check(lib().qcd_measure_async(h, host_out_ptr))
 
 
 def qcd_lattice_destroy(h) -> None:

@@ -561,6 +561,15 @@ int qcd_measure(qcd_lattice* L, double* plaquette, double* polyakov) {
   return measure_impl(L, 1, plaquette, polyakov);
 }
 
+int qcd_measure_async(qcd_lattice* L, double* host_out) {
+  if (int rc = check(L)) return rc;
+  if (!host_out) return set_error(QCD_ERR_INVALID_ARG, "host_out is null");
+  if (int rc = use_device(L)) return rc;
+  QCD_CUDA(L->ops->measure(make_ctx(L, L->seed), 1, L->stream));
+  QCD_CUDA(cudaMemcpyAsync(host_out, L->d_meas, 5 * sizeof(double), cudaMemcpyDeviceToHost, L->stream));
+  return QCD_OK;
+}
+
 int qcd_measure_bare(qcd_lattice* L, double* plaquette) { return measure_impl(L, 0, plaquette, nullptr); }
 
 static size_t canonical_bytes(const qcd_lattice* L) {

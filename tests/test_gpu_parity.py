@@ -351,3 +351,15 @@ def test_reunitarization_of_perturbed_links(q, group, precision):
     unit = np.abs(np.einsum("nki,nkj->nij", M.conj(), M) - np.eye(group)).max()
     assert unit < (1e-14 if precision == FP64_PLAIN else 5e-7)
     lat.close()
+
+
+def test_measure_async_equals_measure(q):
+    import torch
+    lat = q.Lattice(3, 6, 4, 5.9, 1, FP32_COMPRESSED, HOT, 3)
+    lat.sweep(1, 1, 3)
+    out = torch.zeros(5, dtype=torch.float64, pin_memory=True)
+    q.qcd_measure_async(lat.h, out.data_ptr())
+    torch.cuda.synchronize()
+    (p, l) = lat.measure()
+    assert out.tolist() == list(p) + list(l)
+    lat.close()
