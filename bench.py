@@ -460,7 +460,7 @@ def main():
     value = lu_per_step * args.steps * world / (t_ms / 1e3)
 
     # roofline of the dominant kernel (largest share of the timed kernel time)
-    names = ["heatbath_phase", "overrelax_phase", "reunitarize", "measure"]
+    names = ["heatbath_phase", "overrelax_phase", "last_pass_with_reunit", "measure"]
     dom = max(range(2), key=lambda k: prof_ms[k])
     per_launch_ms = prof_ms[dom] / max(1, prof_n[dom])
     link_b = LINK_BYTES[(w.group, 1)]

@@ -127,6 +127,10 @@ int qcd_set_nhit(qcd_lattice *lat, int nhit);
 /* Sweep (sec. 3.3, sec. 5): n_heatbath times { one heat-bath pass; n_overrelax
  * overrelaxation passes; FP64 reunitarization of every link }.  A pass visits
  * the 8 checkerboard phases: parity even then odd, inside it mu = x,y,z,t.
+ * The reunitarization is applied by the last overrelaxation pass's kernels
+ * to each link right after its update in that pass (each link is updated
+ * once per pass), so it costs no separate pass over the links; with
+ * n_overrelax = 0 a reunitarization kernel follows the heat-bath pass.
  * The sweep counter (Philox counter word 1) advances once per heat-bath pass.
  * seed is the Philox key of this call (pass the create seed to continue one
  * stream).  n_heatbath >= 0, n_overrelax >= 0. */
@@ -202,7 +206,10 @@ int qcd_lattice_load(qcd_lattice **out, const char *path, int precision,
  * captured sweep graph), and their durations are accumulated per category:
  *   QCD_PROF_HEATBATH  heat-bath phase kernels
  *   QCD_PROF_OVERRELAX overrelaxation phase kernels
- *   QCD_PROF_REUNIT    reunitarization kernel
+ *   QCD_PROF_REUNIT    the last overrelaxation pass, whose kernels also
+ *                      reunitarize the links they update, and the
+ *                      sweep-counter advance (with n_overrelax = 0: the
+ *                      reunitarization kernel)
  *   QCD_PROF_MEASURE   measurement kernels (block partials + final sum)
  * Enabling or disabling resets the totals.  While enabled, each sweep waits
  * for its own completion before the next is queued.  qcd_get_profile fills

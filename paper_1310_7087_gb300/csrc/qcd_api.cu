@@ -188,9 +188,15 @@ void drop_graphs(qcd_lattice* L) {
   L->graphs.clear();
 }
 
-// One sweep: heat-bath pass, n_or overrelaxation passes, reunitarization that
-// also advances the sweep counter.  With events, event k is recorded before
-// kernel k and the last one after the final kernel.
+__global__ void sweep_advance_kernel(uint32_t* sweep) { *sweep += 1u; }
+
+// One sweep: heat-bath pass, n_or overrelaxation passes, reunitarization, and
+// the advance of the sweep counter.  The reunitarization rides on the last
+// overrelaxation pass (each link is updated once in a pass; that pass's
+// kernels reunitarize it before the store), so no separate pass over the
+// links is needed; with n_or = 0 the reunitarization kernel runs.  With
+// events, event k is recorded before kernel k and the last one after the
+// final kernel.
 int enqueue_sweep(const qcd_lattice* L, const qcd::Ctx& a, int n_or, int block, cudaStream_t st,
                   const std::vector<cudaEvent_t>* events) {
   size_t k = 0;
@@ -208,10 +214,15 @@ int enqueue_sweep(const qcd_lattice* L, const qcd::Ctx& a, int n_or, int block, 
     for (int p = 0; p < 2; ++p)
       for (int mu = 0; mu < 4; ++mu) {
         QCD_CUDA(mark());
-        QCD_CUDA(L->ops->phase(a, qcd::KIND_OR, p, mu, block, st));
+        QCD_CUDA(L->ops->phase(a, o == n_or - 1 ? qcd::KIND_OR_REUNIT : qcd::KIND_OR, p, mu, block, st));
       }
   QCD_CUDA(mark());
-  QCD_CUDA(L->ops->reunit(a, 1, st));
+  if (n_or > 0) {
+    sweep_advance_kernel<<<1, 1, 0, st>>>(a.sweep_rw);
+    QCD_CUDA(cudaGetLastError());
+  } else {
+    QCD_CUDA(L->ops->reunit(a, 1, st));  // no overrelaxation pass to carry it
+  }
   QCD_CUDA(mark());
   return QCD_OK;
 }
@@ -227,9 +238,11 @@ int get_graph(qcd_lattice* L, uint64_t seed, int n_or, SweepGraph** out) {
   SweepGraph sg;
   sg.key = key;
   if (L->profiling) {
+    // buckets: heat-bath pass; overrelaxation passes but the last; the last
+    // pass (it carries the reunitarization) and the counter advance
     const int n_kernels = 8 + 8 * n_or + 1;
     for (int k = 0; k < n_kernels; ++k)
-      sg.kinds.push_back(k < 8 ? QCD_PROF_HEATBATH : (k < n_kernels - 1 ? QCD_PROF_OVERRELAX : QCD_PROF_REUNIT));
+      sg.kinds.push_back(k < 8 ? QCD_PROF_HEATBATH : k < n_kernels - 9 ? QCD_PROF_OVERRELAX : QCD_PROF_REUNIT);
     sg.events.resize(n_kernels + 1, nullptr);
     for (auto& e : sg.events)
       if (cudaEventCreate(&e) != cudaSuccess) {

@@ -50,7 +50,10 @@ inline int meas_poly_blocks(const GeomH& g) {
 }
 inline size_t measure_partials(const GeomH& g) { return 2 * size_t(meas_plaq_blocks(g) + meas_poly_blocks(g)); }
 
-enum { KIND_HB = 0, KIND_OR = 1 };
+// Phase kinds: heat-bath, overrelaxation, and overrelaxation whose kernel also
+// reunitarizes each link it updates before storing it (the last pass of a
+// sweep carries the reunitarization this way, with no pass of its own).
+enum { KIND_HB = 0, KIND_OR = 1, KIND_OR_REUNIT = 2 };
 
 // One table per (group, storage).
 struct PolicyOps {

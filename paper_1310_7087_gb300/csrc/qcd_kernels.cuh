@@ -302,6 +302,12 @@ __device__ __forceinline__ bool frozen_link(const Ctx& a, int mu, int t) {
   return a.field_mode == 1 && mu < 3 && t == 0;
 }
 
+// Reunitarization of one link value (defined with the reunitarization kernels).
+template <typename R>
+__device__ __forceinline__ Quat<R> su2_reunit_value(const Quat<R>& u);
+template <typename R>
+__device__ __forceinline__ void su3_reunit_value(M3<R>& m);
+
 template <typename R, int FIELD, int KIND>
 __global__ void __maxnreg__(QCD_SU3_PHASE_MAXNREG) su3_phase_kernel(const Ctx a, int parity, int mu) {
   using P = SU3Policy<R>;
@@ -357,6 +363,7 @@ __global__ void __maxnreg__(QCD_SU3_PHASE_MAXNREG) su3_phase_kernel(const Ctx a,
     left_rotate(W, r, i, j);
   }
   if (exhausted) atomicAdd(a.exhausted, (unsigned long long)exhausted);
+  if (KIND == KIND_OR_REUNIT) su3_reunit_value<R>(U);
   P::store(a.links, a.g, mu, parity, h, U);
 }
 
@@ -413,10 +420,8 @@ __device__ __forceinline__ double rsqrt1p_minus1(double e) {
   return e * fma(e, fma(e, -0.3125, 0.375), -0.5);
 }
 
-template <typename R, bool CG = false>
-__device__ __forceinline__ void su2_reunit_link(const Ctx& a, int mu, int par, int h) {
-  using P = SU2Policy<R>;
-  const Quat<R> u = P::template load<CG>(a.links, a.g, mu, par, h);
+template <typename R>
+__device__ __forceinline__ Quat<R> su2_reunit_value(const Quat<R>& u) {
   if constexpr (sizeof(R) == 4) {
     // |q|^2 exactly, 1/|q| in FP64, q (1 + (1/|q| - 1)) rounded once in FP32
     Dot2 n;
@@ -427,15 +432,20 @@ __device__ __forceinline__ void su2_reunit_link(const Ctx& a, int mu, int par, i
     const float e = dot2_excess(n);
     const float d = fabsf(e) <= REUNIT_SERIES_MAX ? float(rsqrt1p_minus1(double(e)))
                                                   : float(rsqrt_fp64(n.value()) - 1.0);
-    P::store(a.links, a.g, mu, par, h,
-             Quat<R>{scale1p(u.q0, d), scale1p(u.q1, d), scale1p(u.q2, d), scale1p(u.q3, d)});
+    return Quat<R>{scale1p(u.q0, d), scale1p(u.q1, d), scale1p(u.q2, d), scale1p(u.q3, d)};
   } else {
     const double q0 = u.q0, q1 = u.q1, q2 = u.q2, q3 = u.q3;
     const double nn = fma(q0, q0, fma(q1, q1, fma(q2, q2, q3 * q3)));
     double inv = rsqrt_fp64(nn);
     inv *= fma(-0.5 * nn, inv * inv, 1.5);
-    P::store(a.links, a.g, mu, par, h, Quat<R>{q0 * inv, q1 * inv, q2 * inv, q3 * inv});
+    return Quat<R>{q0 * inv, q1 * inv, q2 * inv, q3 * inv};
   }
+}
+
+template <typename R, bool CG = false>
+__device__ __forceinline__ void su2_reunit_link(const Ctx& a, int mu, int par, int h) {
+  using P = SU2Policy<R>;
+  P::store(a.links, a.g, mu, par, h, su2_reunit_value<R>(P::template load<CG>(a.links, a.g, mu, par, h)));
 }
 
 template <typename R>
@@ -518,6 +528,50 @@ __device__ __forceinline__ void load_rows_fp64(const Ctx& a, int mu, int par, in
   }
 }
 
+// Gram-Schmidt of rows 0-1 and row 2 = conj(row0 x row1), FP64 storage.
+__device__ __forceinline__ void su3d_reunit(M3<double>& d) {
+  double n1 = 0.0;
+#pragma unroll
+  for (int c = 0; c < 3; ++c) n1 = fma(d.e[0][c].re, d.e[0][c].re, fma(d.e[0][c].im, d.e[0][c].im, n1));
+  double i1 = rsqrt_fp64(n1);
+  i1 *= fma(-0.5 * n1, i1 * i1, 1.5);
+#pragma unroll
+  for (int c = 0; c < 3; ++c) d.e[0][c] = scale(d.e[0][c], i1);
+  Cx<double> proj{0.0, 0.0};
+#pragma unroll
+  for (int c = 0; c < 3; ++c) proj = cfma_cn(d.e[0][c], d.e[1][c], proj);
+#pragma unroll
+  for (int c = 0; c < 3; ++c)
+    d.e[1][c] = {fma(-proj.re, d.e[0][c].re, fma(proj.im, d.e[0][c].im, d.e[1][c].re)),
+                 fma(-proj.re, d.e[0][c].im, fma(-proj.im, d.e[0][c].re, d.e[1][c].im))};
+  double n2 = 0.0;
+#pragma unroll
+  for (int c = 0; c < 3; ++c) n2 = fma(d.e[1][c].re, d.e[1][c].re, fma(d.e[1][c].im, d.e[1][c].im, n2));
+  double i2 = rsqrt_fp64(n2);
+  i2 *= fma(-0.5 * n2, i2 * i2, 1.5);
+#pragma unroll
+  for (int c = 0; c < 3; ++c) d.e[1][c] = scale(d.e[1][c], i2);
+  m3_rebuild_row2(d);
+}
+
+// Reunitarized link value: FP32 storage keeps rows 0-1 (row 2 is rebuilt on
+// every load), FP64 storage all three rows.
+template <typename R>
+__device__ __forceinline__ void su3_reunit_value(M3<R>& m) {
+  if constexpr (sizeof(R) == 4) {
+    Cx<float> r[3] = {m.e[0][0], m.e[0][1], m.e[0][2]};
+    Cx<float> t[3] = {m.e[1][0], m.e[1][1], m.e[1][2]};
+    su3f_reunit_rows(r, t);
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      m.e[0][c] = r[c];
+      m.e[1][c] = t[c];
+    }
+  } else {
+    su3d_reunit(m);
+  }
+}
+
 template <typename R, bool CG = false>
 __device__ __forceinline__ void su3_reunit_link(const Ctx& a, int mu, int par, int h) {
   using P = SU3Policy<R>;
@@ -536,28 +590,7 @@ __device__ __forceinline__ void su3_reunit_link(const Ctx& a, int mu, int par, i
   } else {
     M3<double> d;
     load_rows_fp64<CG>(a, mu, par, h, d.e);
-    double n1 = 0.0;
-#pragma unroll
-    for (int c = 0; c < 3; ++c) n1 = fma(d.e[0][c].re, d.e[0][c].re, fma(d.e[0][c].im, d.e[0][c].im, n1));
-    double i1 = rsqrt_fp64(n1);
-    i1 *= fma(-0.5 * n1, i1 * i1, 1.5);
-#pragma unroll
-    for (int c = 0; c < 3; ++c) d.e[0][c] = scale(d.e[0][c], i1);
-    Cx<double> proj{0.0, 0.0};
-#pragma unroll
-    for (int c = 0; c < 3; ++c) proj = cfma_cn(d.e[0][c], d.e[1][c], proj);
-#pragma unroll
-    for (int c = 0; c < 3; ++c)
-      d.e[1][c] = {fma(-proj.re, d.e[0][c].re, fma(proj.im, d.e[0][c].im, d.e[1][c].re)),
-                   fma(-proj.re, d.e[0][c].im, fma(-proj.im, d.e[0][c].re, d.e[1][c].im))};
-    double n2 = 0.0;
-#pragma unroll
-    for (int c = 0; c < 3; ++c) n2 = fma(d.e[1][c].re, d.e[1][c].re, fma(d.e[1][c].im, d.e[1][c].im, n2));
-    double i2 = rsqrt_fp64(n2);
-    i2 *= fma(-0.5 * n2, i2 * i2, 1.5);
-#pragma unroll
-    for (int c = 0; c < 3; ++c) d.e[1][c] = scale(d.e[1][c], i2);
-    m3_rebuild_row2(d);
+    su3d_reunit(d);
     P::store(a.links, a.g, mu, par, h, d);
   }
 }
@@ -892,7 +925,8 @@ inline void launch_phase_level(const Ctx& a, int parity, int mu, int block, cuda
 template <class P>
 cudaError_t launch_phase(const Ctx& a, int kind, int parity, int mu, int block, cudaStream_t st) {
   if (kind == KIND_HB) launch_phase_level<P, KIND_HB>(a, parity, mu, block, st);
-  else launch_phase_level<P, KIND_OR>(a, parity, mu, block, st);
+  else if (kind == KIND_OR) launch_phase_level<P, KIND_OR>(a, parity, mu, block, st);
+  else launch_phase_level<P, KIND_OR_REUNIT>(a, parity, mu, block, st);
   return cudaGetLastError();
 }
 
@@ -964,6 +998,9 @@ int max_phase_block() {
   m = std::min(m, phase_block_limit<P, 0, KIND_OR>());
   m = std::min(m, phase_block_limit<P, 1, KIND_OR>());
   m = std::min(m, phase_block_limit<P, 2, KIND_OR>());
+  m = std::min(m, phase_block_limit<P, 0, KIND_OR_REUNIT>());
+  m = std::min(m, phase_block_limit<P, 1, KIND_OR_REUNIT>());
+  m = std::min(m, phase_block_limit<P, 2, KIND_OR_REUNIT>());
   return m;
 }
 

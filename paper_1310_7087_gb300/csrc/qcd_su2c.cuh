@@ -61,8 +61,13 @@ __device__ __forceinline__ Quat<R> su2c_staple(const Ctx& a, int p, const LexSit
 template <typename R, bool FIELD, int KIND, int MU, bool CG>
 __device__ __forceinline__ void su2c_update(const Ctx& a, int parity, int h, uint32_t sweep) {
   using P = SU2Policy<R>;
+  constexpr bool reunit = KIND == KIND_OR_REUNIT;
   const LexSite x = lex_site(a, parity, h);
   if (frozen_link(a, MU, x.c[3])) return;
+  // a link left as it is still gets the reunitarization the pass carries
+  auto keep = [&]() {
+    if (reunit) P::store(a.links, a.g, MU, parity, h, su2_reunit_value<R>(P::template load<CG>(a.links, a.g, MU, parity, h)));
+  };
   const Quat<R> A = su2c_staple<R, FIELD, MU, CG>(a, parity, x);
   const R k2 = qnorm2(A);
   constexpr bool phased = FIELD && MU == 1;
@@ -81,18 +86,23 @@ __device__ __forceinline__ void su2c_update(const Ctx& a, int parity, int h, uin
       R delta;
       if (!kp_draw<R>(alpha, a.nhit, tries, delta)) {
         atomicAdd(a.exhausted, 1ull);
+        keep();
         return;  // keep the link
       }
       ut_new = qmul(su2_with_delta<R>(delta, dir), qdag(qscale(A, R(1) / k)));
     }
   } else {
-    if (k2 == R(0)) return;
+    if (k2 == R(0)) {
+      keep();
+      return;
+    }
     const Quat<R> Vd = qdag(qscale(A, R(1) / q_sqrt(k2)));
     Quat<R> ut = P::template load<CG>(a.links, a.g, MU, parity, h);
     if (phased) ut = qmul(ut, qdag(Bd));
     ut_new = qmul(qmul(Vd, qdag(ut)), Vd);
   }
-  P::store(a.links, a.g, MU, parity, h, phased ? qmul(ut_new, Bd) : ut_new);
+  const Quat<R> u_new = phased ? qmul(ut_new, Bd) : ut_new;
+  P::store(a.links, a.g, MU, parity, h, reunit ? su2_reunit_value<R>(u_new) : u_new);
 }
 
 template <typename R, bool FIELD, int KIND, int MU>
@@ -119,9 +129,12 @@ cudaError_t su2c_launch_phase(const Ctx& a, int kind, int parity, int mu, int bl
   if (kind == KIND_HB) {
     if (field) su2c_launch_kind<R, true, KIND_HB>(a, parity, mu, block, st);
     else su2c_launch_kind<R, false, KIND_HB>(a, parity, mu, block, st);
-  } else {
+  } else if (kind == KIND_OR) {
     if (field) su2c_launch_kind<R, true, KIND_OR>(a, parity, mu, block, st);
     else su2c_launch_kind<R, false, KIND_OR>(a, parity, mu, block, st);
+  } else {
+    if (field) su2c_launch_kind<R, true, KIND_OR_REUNIT>(a, parity, mu, block, st);
+    else su2c_launch_kind<R, false, KIND_OR_REUNIT>(a, parity, mu, block, st);
   }
   return cudaGetLastError();
 }
@@ -141,8 +154,9 @@ int su2c_limit_mu() {
 
 template <typename R>
 int su2c_max_phase_block() {
-  return std::min(std::min(su2c_limit_mu<R, false, KIND_HB>(), su2c_limit_mu<R, true, KIND_HB>()),
-                  std::min(su2c_limit_mu<R, false, KIND_OR>(), su2c_limit_mu<R, true, KIND_OR>()));
+  const int m = std::min(std::min(su2c_limit_mu<R, false, KIND_HB>(), su2c_limit_mu<R, true, KIND_HB>()),
+                         std::min(su2c_limit_mu<R, false, KIND_OR>(), su2c_limit_mu<R, true, KIND_OR>()));
+  return std::min(m, std::min(su2c_limit_mu<R, false, KIND_OR_REUNIT>(), su2c_limit_mu<R, true, KIND_OR_REUNIT>()));
 }
 
 template <typename R>

@@ -317,6 +317,7 @@ __device__ __forceinline__ void su3c_update(const Ctx& a, int parity, int h, con
     if (sub < 2) su3c_left_rotate(W, r, i, j);
   }
   if (exhausted) atomicAdd(a.exhausted, (unsigned long long)exhausted);
+  if (KIND == KIND_OR_REUNIT) su3_reunit_value<float>(U);
   SU3Policy<float>::store(a.links, a.g, MU, parity, h, U);
 }
 
@@ -356,9 +357,14 @@ inline void su3c_launch_level(const Ctx& a, int parity, int mu, int block, cudaS
   }
 }
 
+// The overrelaxation kernels that also reunitarize (last pass of a sweep) are
+// compiled in their own translation unit.
+cudaError_t su3c_launch_or_reunit(const Ctx& a, int parity, int mu, int block, cudaStream_t st);
+
 inline cudaError_t su3c_launch_phase(const Ctx& a, int kind, int parity, int mu, int block, cudaStream_t st) {
   if (kind == KIND_HB) su3c_launch_level<KIND_HB>(a, parity, mu, block, st);
-  else su3c_launch_level<KIND_OR>(a, parity, mu, block, st);
+  else if (kind == KIND_OR) su3c_launch_level<KIND_OR>(a, parity, mu, block, st);
+  else return su3c_launch_or_reunit(a, parity, mu, block, st);
   return cudaGetLastError();
 }
 
@@ -375,10 +381,13 @@ int su3c_block_limit_mu() {
                   std::min(su3c_block_limit<FIELD, KIND, 2>(), su3c_block_limit<FIELD, KIND, 3>()));
 }
 
+int su3c_or_reunit_max_block();
+
 inline int su3c_max_phase_block() {
   int m = std::min(std::min(su3c_block_limit_mu<0, KIND_HB>(), su3c_block_limit_mu<1, KIND_HB>()),
                    std::min(su3c_block_limit_mu<0, KIND_OR>(), su3c_block_limit_mu<1, KIND_OR>()));
-  return std::min(m, std::min(su3c_block_limit_mu<2, KIND_HB>(), su3c_block_limit_mu<2, KIND_OR>()));
+  m = std::min(m, std::min(su3c_block_limit_mu<2, KIND_HB>(), su3c_block_limit_mu<2, KIND_OR>()));
+  return std::min(m, su3c_or_reunit_max_block());
 }
 
 }  // namespace qcd
