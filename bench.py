@@ -427,9 +427,9 @@ def main():
     h = lat.h
     lu_per_step = (1 + w.n_or) * 4 * w.volume
 
-    def step():
-        q.qcd_sweep(h, 1, w.n_or, seed)
-        return q.qcd_measure(h)
+    def step():  # one working sweep: sweep + measurement (fused into the last OR pass)
+        v = q.qcd_working_sweep(h, 1, w.n_or, seed)
+        return (v[:3], v[3:])
 
     for _ in range(args.warmup):
         step()
@@ -493,8 +493,7 @@ def main():
     results = torch.zeros((e2e_steps, 5), dtype=torch.float64, pin_memory=True)
     for hh in pipe:  # graphs and launch shape in place before timing
         q.qcd_copy_links_in(hh, host.data_ptr(), nbytes)
-        q.qcd_sweep(hh, 1, w.n_or, seed)
-        q.qcd_measure(hh)
+        q.qcd_working_sweep(hh, 1, w.n_or, seed)
     torch.cuda.synchronize()
     if dist:
         dist.barrier()
@@ -502,8 +501,7 @@ def main():
     for i in range(e2e_steps):
         hh = pipe[i % 2]
         q.qcd_copy_links_in(hh, host.data_ptr(), nbytes)
-        q.qcd_sweep(hh, 1, w.n_or, seed)
-        q.qcd_measure_async(hh, results.data_ptr() + i * results.stride(0) * 8)
+        q.qcd_working_sweep(hh, 1, w.n_or, seed, results.data_ptr() + i * results.stride(0) * 8, wait=False)
     torch.cuda.synchronize()
     t_e2e = time.perf_counter() - t0
     assert bool(torch.all(results[:, 0] > 0)), "a pipelined measurement did not arrive"

@@ -136,6 +136,21 @@ int qcd_set_nhit(qcd_lattice *lat, int nhit);
  * stream).  n_heatbath >= 0, n_overrelax >= 0. */
 int qcd_sweep(qcd_lattice *lat, int n_heatbath, int n_overrelax, uint64_t seed);
 
+/* A working sweep (sec. 4: a sweep followed by measurements): n_heatbath
+ * sweeps as qcd_sweep, then the plaquette and Polyakov loop of the resulting
+ * configuration into host_out[5] = {P, P_s, P_t, Re L, Im L} (as
+ * qcd_measure).  With n_overrelax >= 1, FP32 SU(3) storage and the
+ * effective-link field mode, the plaquette sums are fused into the last
+ * overrelaxation pass: after the pass each plaquette of plane (mu, nu < mu)
+ * contains exactly one odd mu-link, so the odd phases mu = 1, 2, 3 add
+ * (1/3) Re Tr(Ut A_nu) for nu < mu over their updated links (A_nu the staples
+ * of plane (mu, nu)) and no separate pass over the links is needed; otherwise
+ * the measurement kernels run after the sweeps.  wait = 1: returns after the
+ * results are on the host; wait = 0: host_out (page-locked for overlap) is
+ * filled once the stream is synchronized. */
+int qcd_working_sweep(qcd_lattice *lat, int n_heatbath, int n_overrelax,
+                      uint64_t seed, double *host_out, int wait);
+
 /* One checkerboard phase (kind QCD_HEATBATH or QCD_OVERRELAX, parity 0/1,
  * direction mu) at the current sweep counter; no reunitarization, no counter
  * change.  For tests and sampled checks. */

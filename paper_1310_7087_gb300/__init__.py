@@ -47,6 +47,7 @@ SIGNATURES = {
     "qcd_reunitarize": (_i, [_vp]),
     "qcd_measure": (_i, [_vp, _P(_d), _P(_d)]),
     "qcd_measure_async": (_i, [_vp, _vp]),
+    "qcd_working_sweep": (_i, [_vp, _i, _i, _u64, _vp, _i]),
     "qcd_measure_bare": (_i, [_vp, _P(_d)]),
     "qcd_get_links": (_i, [_vp, _P(_d)]),
     "qcd_set_links": (_i, [_vp, _P(_d)]),
@@ -160,6 +161,17 @@ def qcd_get_field_mode(h) -> int:
     v = ctypes.c_int()
     _check(lib().qcd_get_field_mode(h, ctypes.byref(v)))
     return v.value
+
+
+def qcd_working_sweep(h, n_heatbath: int, n_overrelax: int, seed: int, host_out_ptr=None, wait: bool = True):
+    """Sweeps and a measurement of the result.  Without host_out_ptr (or with
+    wait) the five results {P, P_s, P_t, Re L, Im L} are returned."""
+    if host_out_ptr is None:
+        out = (ctypes.c_double * 5)()
+        _check(lib().qcd_working_sweep(h, n_heatbath, n_overrelax, seed, ctypes.cast(out, ctypes.c_void_p), 1))
+        return list(out)
+    _check(lib().qcd_working_sweep(h, n_heatbath, n_overrelax, seed, host_out_ptr, 1 if wait else 0))
+    return None
 
 
 def qcd_measure_async(h, host_out_ptr: int) -> None:

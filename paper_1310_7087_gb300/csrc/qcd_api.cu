@@ -9,6 +9,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstdlib>
+#include <algorithm>
 #include <cstring>
 #include <map>
 #include <mutex>
@@ -40,19 +41,21 @@ int set_error(int code, const char* fmt, ...) {
 
 struct GraphKey {
   uint64_t seed;
-  int n_or, nhit, block, profiled;
+  int n_or, nhit, block, profiled, measured;
   bool operator==(const GraphKey& o) const {
-    return seed == o.seed && n_or == o.n_or && nhit == o.nhit && block == o.block && profiled == o.profiled;
+    return seed == o.seed && n_or == o.n_or && nhit == o.nhit && block == o.block && profiled == o.profiled &&
+           measured == o.measured;
   }
 };
 
-// A captured sweep.  When profiled, events[k], events[k + 1] bracket kernel k,
-// whose category is kinds[k].
+// A captured sweep.  When profiled, events[k], events[k + 1] bracket launch
+// slot k (counts[k] kernels), whose category is kinds[k].
 struct SweepGraph {
   GraphKey key;
   cudaGraphExec_t exec = nullptr;
   std::vector<cudaEvent_t> events;
   std::vector<int> kinds;
+  std::vector<int> counts;
 };
 
 // Process-wide autotune cache: (group, precision, Ns, Nt, field, device) ->
@@ -197,7 +200,7 @@ __global__ void sweep_advance_kernel(uint32_t* sweep) { *sweep += 1u; }
 // links is needed; with n_or = 0 the reunitarization kernel runs.  With
 // events, event k is recorded before kernel k and the last one after the
 // final kernel.
-int enqueue_sweep(const qcd_lattice* L, const qcd::Ctx& a, int n_or, int block, cudaStream_t st,
+int enqueue_sweep(const qcd_lattice* L, const qcd::Ctx& a, int n_or, int block, bool measured, cudaStream_t st,
                   const std::vector<cudaEvent_t>* events) {
   size_t k = 0;
   // External event-record nodes: the events stay usable (synchronize, elapsed
@@ -214,7 +217,9 @@ int enqueue_sweep(const qcd_lattice* L, const qcd::Ctx& a, int n_or, int block, 
     for (int p = 0; p < 2; ++p)
       for (int mu = 0; mu < 4; ++mu) {
         QCD_CUDA(mark());
-        QCD_CUDA(L->ops->phase(a, o == n_or - 1 ? qcd::KIND_OR_REUNIT : qcd::KIND_OR, p, mu, block, st));
+        const int kind = o < n_or - 1 ? qcd::KIND_OR
+                         : (measured && p == 1 && mu >= 1) ? qcd::KIND_OR_MEAS : qcd::KIND_OR_REUNIT;
+        QCD_CUDA(L->ops->phase(a, kind, p, mu, block, st));
       }
   QCD_CUDA(mark());
   if (n_or > 0) {
@@ -224,11 +229,15 @@ int enqueue_sweep(const qcd_lattice* L, const qcd::Ctx& a, int n_or, int block, 
     QCD_CUDA(L->ops->reunit(a, 1, st));  // no overrelaxation pass to carry it
   }
   QCD_CUDA(mark());
+  if (measured) {  // Polyakov loop and the final sums of the fused measurement
+    QCD_CUDA(L->ops->measure_fused_tail(a, block, st));
+    QCD_CUDA(mark());
+  }
   return QCD_OK;
 }
 
-int get_graph(qcd_lattice* L, uint64_t seed, int n_or, SweepGraph** out) {
-  const GraphKey key{seed, n_or, L->nhit, L->block, L->profiling};
+int get_graph(qcd_lattice* L, uint64_t seed, int n_or, bool measured, SweepGraph** out) {
+  const GraphKey key{seed, n_or, L->nhit, L->block, L->profiling, measured ? 1 : 0};
   for (auto& g : L->graphs)
     if (g.key == key) {
       *out = &g;
@@ -241,9 +250,15 @@ int get_graph(qcd_lattice* L, uint64_t seed, int n_or, SweepGraph** out) {
     // buckets: heat-bath pass; overrelaxation passes but the last; the last
     // pass (it carries the reunitarization) and the counter advance
     const int n_kernels = 8 + 8 * n_or + 1;
-    for (int k = 0; k < n_kernels; ++k)
+    for (int k = 0; k < n_kernels; ++k) {
       sg.kinds.push_back(k < 8 ? QCD_PROF_HEATBATH : k < n_kernels - 9 ? QCD_PROF_OVERRELAX : QCD_PROF_REUNIT);
-    sg.events.resize(n_kernels + 1, nullptr);
+      sg.counts.push_back(1);
+    }
+    if (measured) {
+      sg.kinds.push_back(QCD_PROF_MEASURE);
+      sg.counts.push_back(2);
+    }
+    sg.events.resize(sg.kinds.size() + 1, nullptr);
     for (auto& e : sg.events)
       if (cudaEventCreate(&e) != cudaSuccess) {
         drop_graph(sg);
@@ -257,7 +272,7 @@ int get_graph(qcd_lattice* L, uint64_t seed, int n_or, SweepGraph** out) {
   cudaError_t e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
   int rc = QCD_OK;
   if (e == cudaSuccess) {
-    rc = enqueue_sweep(L, a, n_or, L->block, cap, L->profiling ? &sg.events : nullptr);
+    rc = enqueue_sweep(L, a, n_or, L->block, measured, cap, L->profiling ? &sg.events : nullptr);
     e = cudaStreamEndCapture(cap, &graph);
   }
   cudaStreamDestroy(cap);
@@ -284,7 +299,7 @@ int fold_profile(qcd_lattice* L, const SweepGraph& g) {
     float ms = 0.f;
     QCD_CUDA(cudaEventElapsedTime(&ms, g.events[k], g.events[k + 1]));
     L->prof_ms[g.kinds[k]] += ms;
-    L->prof_launches[g.kinds[k]] += 1;
+    L->prof_launches[g.kinds[k]] += g.counts[k];
   }
   return QCD_OK;
 }
@@ -432,7 +447,7 @@ int qcd_lattice_create_ex(qcd_lattice** out, int group, int Ns, int Nt, double b
   };
   cudaError_t e = cudaGetDevice(&L->device);
   if (e != cudaSuccess) return fail(set_error(QCD_ERR_CUDA, "cudaGetDevice: %s", cudaGetErrorString(e)));
-  const size_t n_part = qcd::measure_partials(L->g);
+  const size_t n_part = std::max(qcd::measure_partials(L->g), qcd::fused_partials(L->g));
   const size_t small_bytes = 256;
   if (cudaMalloc(&L->links, L->link_bytes) != cudaSuccess ||
       cudaMalloc(reinterpret_cast<void**>(&L->d_small), small_bytes) != cudaSuccess ||
@@ -516,12 +531,41 @@ int qcd_sweep(qcd_lattice* L, int n_heatbath, int n_overrelax, uint64_t seed) {
   if (L->block == 0)
     if (int rc = autotune(L)) return rc;
   SweepGraph* g = nullptr;
-  if (int rc = get_graph(L, seed, n_overrelax, &g)) return rc;
+  if (int rc = get_graph(L, seed, n_overrelax, false, &g)) return rc;
   for (int i = 0; i < n_heatbath; ++i) {
     QCD_CUDA(cudaGraphLaunch(g->exec, L->stream));
     if (L->profiling)
       if (int rc = fold_profile(L, *g)) return rc;
   }
+  return QCD_OK;
+}
+
+static int measure_impl(qcd_lattice* L, int effective, double* plaq, double* poly);
+
+int qcd_working_sweep(qcd_lattice* L, int n_heatbath, int n_overrelax, uint64_t seed, double* host_out, int wait) {
+  if (int rc = check(L)) return rc;
+  if (n_heatbath < 1 || n_overrelax < 0) return set_error(QCD_ERR_INVALID_ARG, "need n_heatbath >= 1, n_overrelax >= 0");
+  if (!host_out) return set_error(QCD_ERR_INVALID_ARG, "host_out is null");
+  if (int rc = use_device(L)) return rc;
+  const bool fused = L->ops->measure_fused_tail && n_overrelax > 0 && L->field_mode == QCD_FIELD_LINKS;
+  if (!fused) {  // separate measurement after the sweeps
+    if (int rc = qcd_sweep(L, n_heatbath, n_overrelax, seed)) return rc;
+    if (wait) return measure_impl(L, 1, host_out, host_out + 3);
+    QCD_CUDA(L->ops->measure(make_ctx(L, L->seed), 1, L->stream));
+    QCD_CUDA(cudaMemcpyAsync(host_out, L->d_meas, 5 * sizeof(double), cudaMemcpyDeviceToHost, L->stream));
+    return QCD_OK;
+  }
+  if (n_heatbath > 1)
+    if (int rc = qcd_sweep(L, n_heatbath - 1, n_overrelax, seed)) return rc;
+  if (L->block == 0)
+    if (int rc = autotune(L)) return rc;
+  SweepGraph* g = nullptr;
+  if (int rc = get_graph(L, seed, n_overrelax, true, &g)) return rc;
+  QCD_CUDA(cudaGraphLaunch(g->exec, L->stream));
+  QCD_CUDA(cudaMemcpyAsync(host_out, L->d_meas, 5 * sizeof(double), cudaMemcpyDeviceToHost, L->stream));
+  if (L->profiling)
+    if (int rc = fold_profile(L, *g)) return rc;
+  if (wait) QCD_CUDA(cudaStreamSynchronize(L->stream));
   return QCD_OK;
 }
 

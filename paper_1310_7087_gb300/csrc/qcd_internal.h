@@ -45,15 +45,27 @@ constexpr int MEAS_THREADS = 256;
 constexpr int FINAL_THREADS = 1024;
 
 inline int meas_plaq_blocks(const GeomH& g) { return int((2LL * g.Vh + MEAS_THREADS - 1) / MEAS_THREADS); }
-inline int meas_poly_blocks(const GeomH& g) {
+__host__ __device__ inline int meas_poly_blocks(const GeomH& g) {
   return int(((long long)g.Ns * g.Ns * g.Ns + MEAS_THREADS - 1) / MEAS_THREADS);
 }
 inline size_t measure_partials(const GeomH& g) { return 2 * size_t(meas_plaq_blocks(g) + meas_poly_blocks(g)); }
+// Measurement fused into a working sweep: the Polyakov-loop partials first,
+// then one stretch per plane-summing phase (mu = 1, 2, 3) of one double per
+// block of the phase kernel (blocks of at least 32 threads).
+__host__ __device__ inline int fused_stride(const GeomH& g) { return (g.Vh + 31) / 32; }
+__host__ __device__ inline int fused_plaq_offset(const GeomH& g, int mu) {
+  return 2 * meas_poly_blocks(g) + (mu - 1) * fused_stride(g);
+}
+inline size_t fused_partials(const GeomH& g) { return size_t(fused_plaq_offset(g, 4)); }
 
 // Phase kinds: heat-bath, overrelaxation, and overrelaxation whose kernel also
 // reunitarizes each link it updates before storing it (the last pass of a
 // sweep carries the reunitarization this way, with no pass of its own).
-enum { KIND_HB = 0, KIND_OR = 1, KIND_OR_REUNIT = 2 };
+// KIND_OR_MEAS: as KIND_OR_REUNIT, and for phase (odd parity, mu >= 1) also
+// sums the plaquettes of the planes (mu, nu < mu) through the updated links:
+// after the last pass each plaquette of plane (mu, nu) has exactly one odd
+// mu-link, so these three phases see every plaquette once.
+enum { KIND_HB = 0, KIND_OR = 1, KIND_OR_REUNIT = 2, KIND_OR_MEAS = 3 };
 
 // One table per (group, storage).
 struct PolicyOps {
@@ -68,6 +80,10 @@ struct PolicyOps {
   cudaError_t (*from_canonical)(const Ctx&, const double* dev_in, cudaStream_t);
   // Frozen-boundary mode: set the spatial links of the t = 0 slice to B.
   cudaError_t (*set_frozen)(const Ctx&, cudaStream_t);
+  // Tail of a working sweep whose last pass ran KIND_OR_MEAS phases with
+  // `block` threads: Polyakov loop and the final sums into meas_out.  Null when
+  // the storage has no fused measurement.
+  cudaError_t (*measure_fused_tail)(const Ctx&, int block, cudaStream_t);
   // Largest block the phase kernels of this storage can launch with (the
   // minimum over heat-bath / overrelaxation, with and without the field).
   int (*max_phase_block)();

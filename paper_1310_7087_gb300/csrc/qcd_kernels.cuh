@@ -926,7 +926,7 @@ template <class P>
 cudaError_t launch_phase(const Ctx& a, int kind, int parity, int mu, int block, cudaStream_t st) {
   if (kind == KIND_HB) launch_phase_level<P, KIND_HB>(a, parity, mu, block, st);
   else if (kind == KIND_OR) launch_phase_level<P, KIND_OR>(a, parity, mu, block, st);
-  else launch_phase_level<P, KIND_OR_REUNIT>(a, parity, mu, block, st);
+  else launch_phase_level<P, KIND_OR_REUNIT>(a, parity, mu, block, st);  // (no fused measurement here)
   return cudaGetLastError();
 }
 
@@ -1016,6 +1016,7 @@ constexpr PolicyOps make_ops(int precision) {
                    &launch_to_canonical<P>,
                    &launch_from_canonical<P>,
                    &launch_set_frozen<P>,
+                   nullptr,
                    &max_phase_block<P>};
 }
 

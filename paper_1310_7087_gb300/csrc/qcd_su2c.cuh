@@ -132,7 +132,7 @@ cudaError_t su2c_launch_phase(const Ctx& a, int kind, int parity, int mu, int bl
   } else if (kind == KIND_OR) {
     if (field) su2c_launch_kind<R, true, KIND_OR>(a, parity, mu, block, st);
     else su2c_launch_kind<R, false, KIND_OR>(a, parity, mu, block, st);
-  } else {
+  } else {  // KIND_OR_REUNIT (no fused measurement for SU(2))
     if (field) su2c_launch_kind<R, true, KIND_OR_REUNIT>(a, parity, mu, block, st);
     else su2c_launch_kind<R, false, KIND_OR_REUNIT>(a, parity, mu, block, st);
   }
@@ -172,6 +172,7 @@ PolicyOps su2c_ops(int precision) {
                    &launch_to_canonical<P>,
                    &launch_from_canonical<P>,
                    &launch_set_frozen<P>,
+                   nullptr,
                    &su2c_max_phase_block<R>};
 }
 

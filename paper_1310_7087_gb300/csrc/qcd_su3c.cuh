@@ -225,14 +225,18 @@ __device__ __forceinline__ Rows2 su3c_eff(const Ctx& a, int par, const LexSite& 
 }
 
 // Staple sum of U_MU(x) (x of parity p) on effective links, full 3x3.
-template <int FIELD, int MU>
-__device__ __forceinline__ M3<float> su3c_staple(const Ctx& a, int p, const LexSite& x) {
+// With SPLIT, *low receives the part of the sum over nu < MU.
+template <int FIELD, int MU, bool SPLIT = false>
+__device__ __forceinline__ M3<float> su3c_staple(const Ctx& a, int p, const LexSite& x, M3<float>* low = nullptr) {
   M3<float> A;
   m3_zero(A);
   const LexSite xp = lex_step<MU, +1>(a.g, x);
 #pragma unroll
   for (int nu = 0; nu < 4; ++nu) {
-    if (nu == MU) continue;
+    if (nu == MU) {
+      if (SPLIT) *low = A;
+      continue;
+    }
     // Each branch of this switch is one static value of NU.
     switch (nu) {
 #define QCD_SU3C_NU(NU)                                                                         \
@@ -261,9 +265,10 @@ __device__ __forceinline__ M3<float> su3c_staple(const Ctx& a, int p, const LexS
 }
 
 // Heat-bath or overrelaxation of U_MU(x) given its staple sum A.
+// Returns the link as stored (rows 0-1; row 2 not kept up to date).
 template <int FIELD, int KIND, int MU>
-__device__ __forceinline__ void su3c_update(const Ctx& a, int parity, int h, const LexSite& x, const M3<float>& A,
-                                            M3<float> U) {
+__device__ __forceinline__ M3<float> su3c_update(const Ctx& a, int parity, int h, const LexSite& x,
+                                                 const M3<float>& A, M3<float> U) {
   M3<float> Ut = U;
   if (FIELD == 2 && MU == 1) {
     Cx<float> b[3];
@@ -317,8 +322,24 @@ __device__ __forceinline__ void su3c_update(const Ctx& a, int parity, int h, con
     if (sub < 2) su3c_left_rotate(W, r, i, j);
   }
   if (exhausted) atomicAdd(a.exhausted, (unsigned long long)exhausted);
-  if (KIND == KIND_OR_REUNIT) su3_reunit_value<float>(U);
+  if (KIND == KIND_OR_REUNIT || KIND == KIND_OR_MEAS) su3_reunit_value<float>(U);
   SU3Policy<float>::store(a.links, a.g, MU, parity, h, U);
+  return U;
+}
+
+// Sum of v over the block (any multiple of 32 threads), in a fixed order,
+// written by thread 0.  Every thread of the block must call it.
+__device__ __forceinline__ void block_sum_any(double v, double* out) {
+  __shared__ double sh[32];
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(0xffffffffu, v, off);
+  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = v;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double s = 0.0;
+    for (int w = 0; w < int(blockDim.x >> 5); ++w) s += sh[w];
+    *out = s;
+  }
 }
 
 template <int FIELD, int KIND, int MU>
@@ -330,6 +351,92 @@ __global__ void __maxnreg__(QCD_SU3_PHASE_MAXNREG) su3c_phase_kernel(const Ctx a
   const int h = x.s >> 1;
   const M3<float> A = su3c_staple<FIELD, MU>(a, parity, x);
   su3c_update<FIELD, KIND, MU>(a, parity, h, x, A, su3c_full(su3c_load(a.links, a.g, MU, parity, h)));
+}
+
+// Last-pass phase (odd parity, MU >= 1) of a working sweep: update and
+// reunitarize as KIND_OR_REUNIT, and sum (1/3) Re Tr(Ut_new S) over the
+// phase, S the staples of the planes (MU, nu < MU): the plaquettes of those
+// planes, each once.  Not used in the frozen-boundary mode.
+// The plane-summing phases keep the partial staple live through the update:
+// 128 registers (measured 0.196 ms per launch at 64^3x16; 0.201 at 112, 0.207
+// at 96 with spills).
+#ifndef QCD_SU3_MEAS_MAXNREG
+#define QCD_SU3_MEAS_MAXNREG 128
+#endif
+
+template <int FIELD, int MU>
+__global__ void __maxnreg__(QCD_SU3_MEAS_MAXNREG) su3c_or_meas_kernel(const Ctx a, int parity) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  double v = 0.0;
+  if (i < a.g.Vh) {
+    const LexSite x = lex_site_ytz(a.g, parity, i);
+    const int h = x.s >> 1;
+    M3<float> low;
+    const M3<float> A = su3c_staple<FIELD, MU, true>(a, parity, x, &low);
+    M3<float> U = su3c_update<FIELD, KIND_OR_MEAS, MU>(a, parity, h, x, A,
+                                                       su3c_full(su3c_load(a.links, a.g, MU, parity, h)));
+    su3c_rebuild(U);  // row 2 as every later load rebuilds it
+    if (FIELD == 1 && MU == 1) {
+      const float2 ph = __ldg(a.phase32 + x.c[0]);
+      const Cx<float> pp{ph.x, ph.y}, pc{ph.x, -ph.y};
+#pragma unroll
+      for (int r = 0; r < 3; ++r) {
+        U.e[r][0] = xy_mul(xy_first(U.e[r][0], pp));
+        U.e[r][1] = xy_mul(xy_first(U.e[r][1], pc));
+      }
+    } else if (FIELD == 2 && MU == 1) {
+      Cx<float> b[3];
+      load_bdiag<float>(a, x.c[0], b);
+#pragma unroll
+      for (int r = 0; r < 3; ++r)
+#pragma unroll
+        for (int k = 0; k < 3; ++k) U.e[r][k] = xy_mul(xy_first(U.e[r][k], b[k]));
+    }
+    v = double(m3_retrace_mul(U, low)) / 3.0;
+  }
+  block_sum_any(v, a.partials + fused_plaq_offset(a.g, MU) + blockIdx.x);
+}
+
+// Final sums of a working sweep's fused measurement: plaquette partials of the
+// three plane-summing phases (each `grid` blocks) and the Polyakov partials.
+static __global__ void __launch_bounds__(FINAL_THREADS) su3c_fused_final_kernel(const Ctx a, int grid) {
+  __shared__ double sh[4][FINAL_THREADS];
+  const int nl = meas_poly_blocks(a.g);
+  double s[4] = {0.0, 0.0, 0.0, 0.0};
+  for (int b = threadIdx.x; b < grid; b += FINAL_THREADS) {
+    s[0] += a.partials[fused_plaq_offset(a.g, 1) + b] + a.partials[fused_plaq_offset(a.g, 2) + b];
+    s[1] += a.partials[fused_plaq_offset(a.g, 3) + b];
+  }
+  for (int b = threadIdx.x; b < nl; b += FINAL_THREADS) {
+    s[2] += a.partials[2 * b];
+    s[3] += a.partials[2 * b + 1];
+  }
+#pragma unroll
+  for (int k = 0; k < 4; ++k) sh[k][threadIdx.x] = s[k];
+  __syncthreads();
+  for (int w = FINAL_THREADS / 2; w > 0; w >>= 1) {
+    if (int(threadIdx.x) < w) {
+#pragma unroll
+      for (int k = 0; k < 4; ++k) sh[k][threadIdx.x] += sh[k][threadIdx.x + w];
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    const double V = 2.0 * double(a.g.Vh);
+    const double V3 = double(a.g.Ns) * a.g.Ns * a.g.Ns;
+    a.meas_out[0] = (sh[0][0] + sh[1][0]) / (6.0 * V);
+    a.meas_out[1] = sh[0][0] / (3.0 * V);
+    a.meas_out[2] = sh[1][0] / (3.0 * V);
+    a.meas_out[3] = sh[2][0] / V3;
+    a.meas_out[4] = sh[3][0] / V3;
+  }
+}
+
+inline cudaError_t su3c_measure_fused_tail(const Ctx& a, int block, cudaStream_t st) {
+  const int nl = meas_poly_blocks(a.g);
+  measure_kernel<SU3Policy<float>, 0><<<nl, MEAS_THREADS, 0, st>>>(a, 0);  // Polyakov loop only
+  su3c_fused_final_kernel<<<1, FINAL_THREADS, 0, st>>>(a, int(grid_for(a.g.Vh, block)));
+  return cudaGetLastError();
 }
 
 template <int FIELD, int KIND, int MU>
@@ -357,13 +464,16 @@ inline void su3c_launch_level(const Ctx& a, int parity, int mu, int block, cudaS
   }
 }
 
-// The overrelaxation kernels that also reunitarize (last pass of a sweep) are
-// compiled in their own translation unit.
+// The overrelaxation kernels that also reunitarize (last pass of a sweep),
+// with or without the fused plaquette sums, are compiled in their own
+// translation unit.
 cudaError_t su3c_launch_or_reunit(const Ctx& a, int parity, int mu, int block, cudaStream_t st);
+cudaError_t su3c_launch_or_meas(const Ctx& a, int parity, int mu, int block, cudaStream_t st);
 
 inline cudaError_t su3c_launch_phase(const Ctx& a, int kind, int parity, int mu, int block, cudaStream_t st) {
   if (kind == KIND_HB) su3c_launch_level<KIND_HB>(a, parity, mu, block, st);
   else if (kind == KIND_OR) su3c_launch_level<KIND_OR>(a, parity, mu, block, st);
+  else if (kind == KIND_OR_MEAS && mu >= 1) return su3c_launch_or_meas(a, parity, mu, block, st);
   else return su3c_launch_or_reunit(a, parity, mu, block, st);
   return cudaGetLastError();
 }

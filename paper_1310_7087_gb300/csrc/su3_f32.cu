@@ -15,5 +15,6 @@ const PolicyOps kOpsSU3F32 = PolicyOps{3,
                                        &launch_to_canonical<SU3F>,
                                        &launch_from_canonical<SU3F>,
                                        &launch_set_frozen<SU3F>,
+                                       &su3c_measure_fused_tail,
                                        &su3c_max_phase_block};
 }  // namespace qcd

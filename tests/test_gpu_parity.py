@@ -363,3 +363,36 @@ def test_measure_async_equals_measure(q):
     (p, l) = lat.measure()
     assert out.tolist() == list(p) + list(l)
     lat.close()
+
+
+@pytest.mark.parametrize("group,precision,flux,flux8,mode", [
+    (3, FP32_COMPRESSED, 1, 0, 0), (3, FP32_COMPRESSED, 0, 0, 0), (3, FP32_COMPRESSED, 1, 1, 0),
+    (3, FP32_COMPRESSED, 1, 0, 1), (3, FP64_PLAIN, 1, 0, 0), (2, FP32_COMPRESSED, 1, 0, 0)])
+def test_working_sweep_equals_sweep_then_measure(q, group, precision, flux, flux8, mode):
+    """qcd_working_sweep (measurement fused into the last overrelaxation pass
+    where available) gives the links of qcd_sweep and the measurement of
+    qcd_measure on them."""
+    Ns, Nt, beta = 6, 4, (5.8 if group == 3 else 2.3)
+    a = q.Lattice(group, Ns, Nt, beta, flux, precision, HOT, 5, field_mode=mode, flux8=flux8)
+    b = q.Lattice(group, Ns, Nt, beta, flux, precision, HOT, 5, field_mode=mode, flux8=flux8)
+    for n_hb, n_or in ((1, 4), (2, 1), (1, 0)):
+        got = q.qcd_working_sweep(a.h, n_hb, n_or, 5)
+        b.sweep(n_hb, n_or, 5)
+        assert np.array_equal(a.get_links(), b.get_links())
+        (p, l) = b.measure()
+        tol = 1e-12 if precision == FP64_PLAIN else 1e-6
+        assert np.abs(np.array(got) - np.array(list(p) + list(l))).max() <= tol, (got, p, l)
+    a.close()
+    b.close()
+
+
+def test_working_sweep_matches_oracle_measure(q):
+    """Fused measurement on a 16^3 x 4 FP32 lattice against the oracle's
+    measurement of the same configuration."""
+    lat = q.Lattice(3, 16, 4, 5.9, 1, FP32_COMPRESSED, HOT, 9)
+    got = q.qcd_working_sweep(lat.h, 1, 2, 9)
+    orc = oracle.OracleLattice(3, 16, 4, 5.9, 1, 10, 0)
+    orc.set_links(lat.get_links())
+    (op, ol) = orc.measure()
+    assert np.abs(np.array(got) - np.array(list(op) + list(ol))).max() <= 1e-6, (got, op, ol)
+    lat.close()
