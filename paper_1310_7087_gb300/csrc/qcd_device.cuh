@@ -271,6 +271,26 @@ __device__ __forceinline__ bool kp_draw(R alpha, int nhit, const Stream& st, R& 
   return false;
 }
 
+// FP32: the same draw with the hardware logarithm and cosine.  Their absolute
+// errors (about 2^-21) move delta by less than 1e-7 / alpha, below the FP32
+// resolution of a0 = 1 - delta; cos^2 is taken at 2 pi (u - 1/2), inside the
+// fast cosine's accurate range, which leaves cos^2 unchanged.
+template <>
+__device__ __forceinline__ bool kp_draw<float>(float alpha, int nhit, const Stream& st, float& delta) {
+  const float inv_alpha = 1.f / alpha;
+  for (int t = 0; t < nhit; ++t) {
+    float u[4];
+    st.uniforms<float>(uint32_t(t), u);
+    const float c = __cosf(6.283185307179586f * (u[2] - 0.5f));
+    const float d = (-__logf(u[1]) - __logf(u[0]) * c * c) * inv_alpha;
+    if (u[3] * u[3] <= 1.f - 0.5f * d) {
+      delta = d;
+      return true;
+    }
+  }
+  return false;
+}
+
 // Unit quaternion with real part a0 = 1 - delta and a direction uniform on
 // S^2 from block 0 of the direction stream: cos(theta) = 2 u1 - 1,
 // phi = 2 pi u2.  The moduli use the cancellation-free forms
@@ -286,6 +306,20 @@ __device__ __forceinline__ Quat<R> su2_with_delta(R delta, const Stream& dir) {
   q_sincospi(R(2) * u[1], &sp, &cp);
   const R r = q_sqrt(delta * (R(2) - delta));
   return {R(1) - delta, r * st * cp, r * st * sp, r * ct};
+}
+
+// FP32: the azimuth's sine and cosine from the hardware pair at
+// 2 pi (u - 1/2) (both change sign against 2 pi u).
+template <>
+__device__ __forceinline__ Quat<float> su2_with_delta<float>(float delta, const Stream& dir) {
+  float u[4];
+  dir.uniforms<float>(0u, u);
+  const float ct = 2.f * u[0] - 1.f;
+  const float st = 2.f * sqrtf(u[0] * (1.f - u[0]));
+  float sp, cp;
+  __sincosf(6.283185307179586f * (u[1] - 0.5f), &sp, &cp);
+  const float r = sqrtf(delta * (2.f - delta));
+  return {1.f - delta, -r * st * cp, -r * st * sp, r * ct};
 }
 
 // Haar-random unit quaternion (Shoemake) from one block.

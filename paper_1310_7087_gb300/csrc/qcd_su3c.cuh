@@ -311,7 +311,7 @@ __device__ __forceinline__ M3<float> su3c_update(const Ctx& a, int parity, int h
           continue;
         }
         const Quat<float> X = su2_with_delta<float>(delta, dir);
-        r = qmul(X, qdag(qscale(w, 1.f / k)));
+        r = qmul(X, qdag(qscale(w, rsqrtf(n2))));
       }
     } else {
       if (n2 == 0.f) continue;
