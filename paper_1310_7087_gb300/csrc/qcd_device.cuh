@@ -277,7 +277,7 @@ __device__ __forceinline__ bool kp_draw(R alpha, int nhit, const Stream& st, R& 
 // fast cosine's accurate range, which leaves cos^2 unchanged.
 template <>
 __device__ __forceinline__ bool kp_draw<float>(float alpha, int nhit, const Stream& st, float& delta) {
-  const float inv_alpha = 1.f / alpha;
+  const float inv_alpha = __fdividef(1.f, alpha);
   for (int t = 0; t < nhit; ++t) {
     float u[4];
     st.uniforms<float>(uint32_t(t), u);
@@ -309,16 +309,20 @@ __device__ __forceinline__ Quat<R> su2_with_delta(R delta, const Stream& dir) {
 }
 
 // FP32: the azimuth's sine and cosine from the hardware pair at
-// 2 pi (u - 1/2) (both change sign against 2 pi u).
+// 2 pi (u - 1/2) (both change sign against 2 pi u), approximate square roots.
 template <>
 __device__ __forceinline__ Quat<float> su2_with_delta<float>(float delta, const Stream& dir) {
   float u[4];
   dir.uniforms<float>(0u, u);
+  // square roots as x rsqrt(x): both arguments are positive (u0 in (0, 1),
+  // delta > 0 since -ln u > 0 for every uniform)
   const float ct = 2.f * u[0] - 1.f;
-  const float st = 2.f * sqrtf(u[0] * (1.f - u[0]));
+  const float q = u[0] * (1.f - u[0]);
+  const float st = 2.f * q * rsqrtf(q);
   float sp, cp;
   __sincosf(6.283185307179586f * (u[1] - 0.5f), &sp, &cp);
-  const float r = sqrtf(delta * (2.f - delta));
+  const float e = delta * (2.f - delta);
+  const float r = e * rsqrtf(e);
   return {1.f - delta, -r * st * cp, -r * st * sp, r * ct};
 }
 

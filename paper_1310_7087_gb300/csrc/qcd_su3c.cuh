@@ -298,7 +298,8 @@ __device__ __forceinline__ M3<float> su3c_update(const Ctx& a, int parity, int h
     const float n2 = qnorm2(w);
     Quat<float> r;
     if (KIND == KIND_HB) {
-      const float k = sqrtf(n2);
+      const float rk = n2 > 0.f ? rsqrtf(n2) : 0.f;  // 1/k (approximate, ~2 ulp)
+      const float k = n2 * rk;
       const float alpha = float(2.0 / 3.0) * float(a.beta) * k;
       const Stream dir = make_stream(a.k0, a.k1, uint32_t(x.s), sweep, MU, sub, KIND_DIR);
       if (alpha == 0.f) {
@@ -311,7 +312,7 @@ __device__ __forceinline__ M3<float> su3c_update(const Ctx& a, int parity, int h
           continue;
         }
         const Quat<float> X = su2_with_delta<float>(delta, dir);
-        r = qmul(X, qdag(qscale(w, rsqrtf(n2))));
+        r = qmul(X, qdag(qscale(w, rk)));
       }
     } else {
       if (n2 == 0.f) continue;
