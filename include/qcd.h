@@ -226,10 +226,13 @@ int qcd_lattice_load(qcd_lattice **out, const char *path, int precision,
  *                      sweep-counter advance (with n_overrelax = 0: the
  *                      reunitarization kernel)
  *   QCD_PROF_MEASURE   measurement kernels (block partials + final sum)
- * Enabling or disabling resets the totals.  While enabled, each sweep waits
- * for its own completion before the next is queued.  qcd_get_profile fills
- * ms[QCD_PROF_N] (total milliseconds) and launches[QCD_PROF_N]; it
- * synchronizes the stream. */
+ * Events bracket groups of kernels (the heat-bath pass, the other
+ * overrelaxation passes, the last pass, the measurement), and a group's time
+ * is counted for all its kernels.  Enabling or disabling resets the totals.
+ * Sweeps stay queued back to back: two instances of each captured sweep
+ * alternate and one instance's events are read before its next launch.
+ * qcd_get_profile fills ms[QCD_PROF_N] (total milliseconds) and
+ * launches[QCD_PROF_N]; it synchronizes the stream. */
 #define QCD_PROF_HEATBATH 0
 #define QCD_PROF_OVERRELAX 1
 #define QCD_PROF_REUNIT 2

@@ -41,21 +41,25 @@ int set_error(int code, const char* fmt, ...) {
 
 struct GraphKey {
   uint64_t seed;
-  int n_or, nhit, block, profiled, measured;
+  int n_or, nhit, block, profiled, measured, instance;
   bool operator==(const GraphKey& o) const {
     return seed == o.seed && n_or == o.n_or && nhit == o.nhit && block == o.block && profiled == o.profiled &&
-           measured == o.measured;
+           measured == o.measured && instance == o.instance;
   }
 };
 
-// A captured sweep.  When profiled, events[k], events[k + 1] bracket launch
-// slot k (counts[k] kernels), whose category is kinds[k].
+// A captured sweep.  When profiled, events[k], events[k + 1] bracket group k
+// of counts[k] kernels of category kinds[k]; `pending` marks a launch whose
+// events have not been read yet.  Two instances of a profiled graph alternate,
+// so reading one launch's events waits for the launch before the previous one
+// (normally long finished) and the sweeps stay queued back to back.
 struct SweepGraph {
   GraphKey key;
   cudaGraphExec_t exec = nullptr;
   std::vector<cudaEvent_t> events;
   std::vector<int> kinds;
   std::vector<int> counts;
+  bool pending = false;
 };
 
 // Process-wide autotune cache: (group, precision, Ns, Nt, field, device) ->
@@ -116,6 +120,7 @@ struct qcd_lattice {
   float2* d_phase32 = nullptr;
   std::vector<SweepGraph> graphs;
   int profiling = 0;
+  int prof_flip = 0;  // alternates the two instances of a profiled graph
   double prof_ms[QCD_PROF_N] = {0, 0, 0, 0};
   unsigned long long prof_launches[QCD_PROF_N] = {0, 0, 0, 0};
   cudaEvent_t meas_ev[2] = {nullptr, nullptr};
@@ -208,20 +213,22 @@ int enqueue_sweep(const qcd_lattice* L, const qcd::Ctx& a, int n_or, int block, 
   auto mark = [&]() -> cudaError_t {
     return events ? cudaEventRecordWithFlags((*events)[k++], st, cudaEventRecordExternal) : cudaSuccess;
   };
+  // event groups: heat-bath pass | overrelaxation passes but the last | last
+  // pass and the counter advance (or the reunitarization kernel) | measurement tail
+  QCD_CUDA(mark());
   for (int p = 0; p < 2; ++p)
-    for (int mu = 0; mu < 4; ++mu) {
-      QCD_CUDA(mark());
-      QCD_CUDA(L->ops->phase(a, qcd::KIND_HB, p, mu, block, st));
-    }
-  for (int o = 0; o < n_or; ++o)
+    for (int mu = 0; mu < 4; ++mu) QCD_CUDA(L->ops->phase(a, qcd::KIND_HB, p, mu, block, st));
+  for (int o = 0; o < n_or; ++o) {
+    if (o == 0 && n_or > 1) QCD_CUDA(mark());
+    if (o == n_or - 1) QCD_CUDA(mark());
     for (int p = 0; p < 2; ++p)
       for (int mu = 0; mu < 4; ++mu) {
-        QCD_CUDA(mark());
         const int kind = o < n_or - 1 ? qcd::KIND_OR
                          : (measured && p == 1 && mu >= 1) ? qcd::KIND_OR_MEAS : qcd::KIND_OR_REUNIT;
         QCD_CUDA(L->ops->phase(a, kind, p, mu, block, st));
       }
-  QCD_CUDA(mark());
+  }
+  if (n_or == 0) QCD_CUDA(mark());
   if (n_or > 0) {
     sweep_advance_kernel<<<1, 1, 0, st>>>(a.sweep_rw);
     QCD_CUDA(cudaGetLastError());
@@ -236,24 +243,33 @@ int enqueue_sweep(const qcd_lattice* L, const qcd::Ctx& a, int n_or, int block, 
   return QCD_OK;
 }
 
+int fold_all(qcd_lattice* L);
+
 int get_graph(qcd_lattice* L, uint64_t seed, int n_or, bool measured, SweepGraph** out) {
-  const GraphKey key{seed, n_or, L->nhit, L->block, L->profiling, measured ? 1 : 0};
+  const int instance = L->profiling ? (L->prof_flip ^= 1) : 0;
+  const GraphKey key{seed, n_or, L->nhit, L->block, L->profiling, measured ? 1 : 0, instance};
   for (auto& g : L->graphs)
     if (g.key == key) {
       *out = &g;
       return QCD_OK;
     }
-  if (L->graphs.size() >= 8) drop_graphs(L);
+  if (L->graphs.size() >= 8) {
+    if (int rc = fold_all(L)) return rc;  // keep the profile of launches in flight
+    drop_graphs(L);
+  }
   SweepGraph sg;
   sg.key = key;
   if (L->profiling) {
     // buckets: heat-bath pass; overrelaxation passes but the last; the last
     // pass (it carries the reunitarization) and the counter advance
-    const int n_kernels = 8 + 8 * n_or + 1;
-    for (int k = 0; k < n_kernels; ++k) {
-      sg.kinds.push_back(k < 8 ? QCD_PROF_HEATBATH : k < n_kernels - 9 ? QCD_PROF_OVERRELAX : QCD_PROF_REUNIT);
-      sg.counts.push_back(1);
+    sg.kinds.push_back(QCD_PROF_HEATBATH);
+    sg.counts.push_back(8);
+    if (n_or > 1) {
+      sg.kinds.push_back(QCD_PROF_OVERRELAX);
+      sg.counts.push_back(8 * (n_or - 1));
     }
+    sg.kinds.push_back(QCD_PROF_REUNIT);
+    sg.counts.push_back(n_or > 0 ? 9 : 1);
     if (measured) {
       sg.kinds.push_back(QCD_PROF_MEASURE);
       sg.counts.push_back(2);
@@ -293,7 +309,9 @@ int get_graph(qcd_lattice* L, uint64_t seed, int n_or, bool measured, SweepGraph
 }
 
 // Add the durations bracketed by a completed profiled graph's events.
-int fold_profile(qcd_lattice* L, const SweepGraph& g) {
+int fold_profile(qcd_lattice* L, SweepGraph& g) {
+  if (!g.pending) return QCD_OK;
+  g.pending = false;
   QCD_CUDA(cudaEventSynchronize(g.events.back()));
   for (size_t k = 0; k + 1 < g.events.size(); ++k) {
     float ms = 0.f;
@@ -301,6 +319,21 @@ int fold_profile(qcd_lattice* L, const SweepGraph& g) {
     L->prof_ms[g.kinds[k]] += ms;
     L->prof_launches[g.kinds[k]] += g.counts[k];
   }
+  return QCD_OK;
+}
+
+int fold_all(qcd_lattice* L) {
+  for (auto& g : L->graphs)
+    if (int rc = fold_profile(L, g)) return rc;
+  return QCD_OK;
+}
+
+// Launch a captured sweep; a profiled one first reads the events of this
+// instance's previous launch.
+int launch_graph(qcd_lattice* L, SweepGraph& g) {
+  if (int rc = fold_profile(L, g)) return rc;
+  QCD_CUDA(cudaGraphLaunch(g.exec, L->stream));
+  g.pending = L->profiling != 0;
   return QCD_OK;
 }
 
@@ -533,9 +566,9 @@ int qcd_sweep(qcd_lattice* L, int n_heatbath, int n_overrelax, uint64_t seed) {
   SweepGraph* g = nullptr;
   if (int rc = get_graph(L, seed, n_overrelax, false, &g)) return rc;
   for (int i = 0; i < n_heatbath; ++i) {
-    QCD_CUDA(cudaGraphLaunch(g->exec, L->stream));
-    if (L->profiling)
-      if (int rc = fold_profile(L, *g)) return rc;
+    if (i > 0 && L->profiling)
+      if (int rc = get_graph(L, seed, n_overrelax, false, &g)) return rc;  // the other instance
+    if (int rc = launch_graph(L, *g)) return rc;
   }
   return QCD_OK;
 }
@@ -561,10 +594,8 @@ int qcd_working_sweep(qcd_lattice* L, int n_heatbath, int n_overrelax, uint64_t 
     if (int rc = autotune(L)) return rc;
   SweepGraph* g = nullptr;
   if (int rc = get_graph(L, seed, n_overrelax, true, &g)) return rc;
-  QCD_CUDA(cudaGraphLaunch(g->exec, L->stream));
+  if (int rc = launch_graph(L, *g)) return rc;
   QCD_CUDA(cudaMemcpyAsync(host_out, L->d_meas, 5 * sizeof(double), cudaMemcpyDeviceToHost, L->stream));
-  if (L->profiling)
-    if (int rc = fold_profile(L, *g)) return rc;
   if (wait) QCD_CUDA(cudaStreamSynchronize(L->stream));
   return QCD_OK;
 }
@@ -720,6 +751,7 @@ int qcd_set_profiling(qcd_lattice* L, int enable) {
   QCD_CUDA(L->stream ? cudaStreamSynchronize(L->stream) : cudaDeviceSynchronize());
   for (auto& e : L->meas_ev)
     if (!e) QCD_CUDA(cudaEventCreate(&e));
+  for (auto& g : L->graphs) g.pending = false;  // totals restart
   L->profiling = enable ? 1 : 0;
   for (int k = 0; k < QCD_PROF_N; ++k) {
     L->prof_ms[k] = 0.0;
@@ -733,6 +765,7 @@ int qcd_get_profile(qcd_lattice* L, double* ms, unsigned long long* launches) {
   if (!ms || !launches) return set_error(QCD_ERR_INVALID_ARG, "null output");
   if (int rc = use_device(L)) return rc;
   QCD_CUDA(cudaStreamSynchronize(L->stream));
+  if (int rc = fold_all(L)) return rc;
   for (int k = 0; k < QCD_PROF_N; ++k) {
     ms[k] = L->prof_ms[k];
     launches[k] = L->prof_launches[k];

@@ -396,3 +396,26 @@ def test_working_sweep_matches_oracle_measure(q):
     (op, ol) = orc.measure()
     assert np.abs(np.array(got) - np.array(list(op) + list(ol))).max() <= 1e-6, (got, op, ol)
     lat.close()
+
+
+def test_live_profile_counts_every_kernel(q):
+    """Live profile over sweeps and working sweeps: launches per category as
+    the sweep schedule has them, positive times, sum within the wall time."""
+    import torch
+    lat = q.Lattice(3, 8, 4, 5.9, 1, FP32_COMPRESSED, HOT, 3)
+    lat.sweep(1, 4, 3)
+    q.qcd_set_profiling(lat.h, True)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record()
+    lat.sweep(3, 4, 3)
+    for _ in range(2):
+        q.qcd_working_sweep(lat.h, 1, 4, 3)
+    e1.record()
+    torch.cuda.synchronize()
+    ms, n = q.qcd_get_profile(lat.h)
+    q.qcd_set_profiling(lat.h, False)
+    assert list(n) == [5 * 8, 5 * 24, 5 * 9, 2 * 2], n
+    assert all(m > 0 for m in ms)
+    assert sum(ms) <= e0.elapsed_time(e1) * 1.001
+    lat.close()
