@@ -120,11 +120,14 @@ __device__ __forceinline__ void block_sum4(double v[4], double* out) {
 
 // One phase of one lattice, this CTA's share of its sites.
 template <typename R, bool FIELD, int KIND>
-__device__ __forceinline__ void batch_phase(const Ctx& a, int p, int mu, int first, int stride, uint32_t sweep) {
+// One phase over this CTA's share of the lattice; returns the sum of the
+// updates' plaquette terms (KIND_OR_MEAS) in FP64.
+__device__ __forceinline__ double batch_phase(const Ctx& a, int p, int mu, int first, int stride, uint32_t sweep) {
+  double v = 0.0;
   switch (mu) {
-#define QCD_BATCH_MU(MU)                                                                         \
-  case MU:                                                                                       \
-    for (int h = first; h < a.g.Vh; h += stride) su2c_update<R, FIELD, KIND, MU, true>(a, p, h, sweep); \
+#define QCD_BATCH_MU(MU)                                                                          \
+  case MU:                                                                                        \
+    for (int h = first; h < a.g.Vh; h += stride) v += double(su2c_update<R, FIELD, KIND, MU, true>(a, p, h, sweep)); \
     break;
     QCD_BATCH_MU(0)
     QCD_BATCH_MU(1)
@@ -132,6 +135,7 @@ __device__ __forceinline__ void batch_phase(const Ctx& a, int p, int mu, int fir
     QCD_BATCH_MU(3)
 #undef QCD_BATCH_MU
   }
+  return v;
 }
 
 template <typename R, bool FIELD>
@@ -171,19 +175,29 @@ __device__ void batch_run(const BatchArgs& b, int li, const BatchLat& L, int j) 
         batch_phase<R, FIELD, KIND_HB>(a, p, mu, first, stride, sweep);
         if (!barrier()) return;
       }
+    double v[4] = {0.0, 0.0, 0.0, 0.0};
+    // the last OR pass reunitarizes the links it updates and its odd phases
+    // mu = 1..3 sum the plaquettes of the planes (mu, nu < mu), each once
     for (int o = 0; o < b.n_or; ++o)
       for (int p = 0; p < 2; ++p)
         for (int mu = 0; mu < 4; ++mu) {
-          batch_phase<R, FIELD, KIND_OR>(a, p, mu, first, stride, sweep);
+          if (o < b.n_or - 1) {
+            batch_phase<R, FIELD, KIND_OR>(a, p, mu, first, stride, sweep);
+          } else if (p == 1 && mu >= 1) {
+            v[mu == 3 ? 1 : 0] += batch_phase<R, FIELD, KIND_OR_MEAS>(a, p, mu, first, stride, sweep);
+          } else {
+            batch_phase<R, FIELD, KIND_OR_REUNIT>(a, p, mu, first, stride, sweep);
+          }
           if (!barrier()) return;
         }
-    for (int64_t idx = first; idx < 4 * V; idx += stride) {
-      const int plane = int(idx / L.Vh), h = int(idx % L.Vh);
-      su2_reunit_link<R, true>(a, plane >> 1, plane & 1, h);
+    if (b.n_or == 0) {  // no OR pass to carry them: reunitarization and plaquettes on their own
+      for (int64_t idx = first; idx < 4 * V; idx += stride) {
+        const int plane = int(idx / L.Vh), h = int(idx % L.Vh);
+        su2_reunit_link<R, true>(a, plane >> 1, plane & 1, h);
+      }
+      if (!barrier()) return;
+      for (int64_t idx = first; idx < V; idx += stride) plaquette_site<P, FIELD, true>(a, idx, v[0], v[1]);
     }
-    if (!barrier()) return;
-    double v[4] = {0.0, 0.0, 0.0, 0.0};
-    for (int64_t idx = first; idx < V; idx += stride) plaquette_site<P, FIELD, true>(a, idx, v[0], v[1]);
     for (int64_t idx = first; idx < V3; idx += stride) polyakov_site<P, true>(a, idx, v[2], v[3]);
     block_sum4(v, b.partials + 4 * int64_t(blockIdx.x));
     if (!barrier()) return;

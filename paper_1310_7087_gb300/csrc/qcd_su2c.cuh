@@ -21,14 +21,18 @@ __device__ __forceinline__ Quat<R> su2c_eff(const Ctx& a, int par, const LexSite
   return u;
 }
 
-// Staple sum of U_MU(x), x of parity p, on effective links (quaternion form).
-template <typename R, bool FIELD, int MU, bool CG>
-__device__ __forceinline__ Quat<R> su2c_staple(const Ctx& a, int p, const LexSite& x) {
+// Staple sum of U_MU(x), x of parity p, on effective links (quaternion form);
+// with SPLIT, *low receives the part over nu < MU.
+template <typename R, bool FIELD, int MU, bool CG, bool SPLIT = false>
+__device__ __forceinline__ Quat<R> su2c_staple(const Ctx& a, int p, const LexSite& x, Quat<R>* low = nullptr) {
   Quat<R> A{R(0), R(0), R(0), R(0)};
   const LexSite xp = lex_step<MU, +1>(a.g, x);
 #pragma unroll
   for (int nu = 0; nu < 4; ++nu) {
-    if (nu == MU) continue;
+    if (nu == MU) {
+      if (SPLIT) *low = A;
+      continue;
+    }
     switch (nu) {
 #define QCD_SU2C_NU(NU)                                                                       \
   case NU: {                                                                                    \
@@ -57,28 +61,32 @@ __device__ __forceinline__ Quat<R> su2c_staple(const Ctx& a, int p, const LexSit
 
 // One link update: A = k V (k = sqrt(det A)); heat-bath Ut_new = X V^+ with X
 // drawn by Kennedy-Pendleton (Haar when alpha = beta k = 0), overrelaxation
-// Ut_new = V^+ Ut^+ V^+; stored U = Ut_new B^+.
+// Ut_new = V^+ Ut^+ V^+; stored U = Ut_new B^+.  KIND_OR_REUNIT and
+// KIND_OR_MEAS reunitarize the stored link; KIND_OR_MEAS (odd parity, MU >= 1
+// of a working sweep's last pass) returns (1/2) Re Tr(Ut A_nu) summed over
+// nu < MU for the final link, i.e. the plaquettes of the planes (MU, nu < MU)
+// through it.
 template <typename R, bool FIELD, int KIND, int MU, bool CG>
-__device__ __forceinline__ void su2c_update(const Ctx& a, int parity, int h, uint32_t sweep) {
+__device__ __forceinline__ R su2c_update(const Ctx& a, int parity, int h, uint32_t sweep) {
   using P = SU2Policy<R>;
-  constexpr bool reunit = KIND == KIND_OR_REUNIT;
+  constexpr bool reunit = KIND == KIND_OR_REUNIT || KIND == KIND_OR_MEAS;
+  constexpr bool meas = KIND == KIND_OR_MEAS;
   const LexSite x = lex_site(a, parity, h);
-  if (frozen_link(a, MU, x.c[3])) return;
-  // a link left as it is still gets the reunitarization the pass carries
-  auto keep = [&]() {
-    if (reunit) P::store(a.links, a.g, MU, parity, h, su2_reunit_value<R>(P::template load<CG>(a.links, a.g, MU, parity, h)));
-  };
-  const Quat<R> A = su2c_staple<R, FIELD, MU, CG>(a, parity, x);
+  if (frozen_link(a, MU, x.c[3])) return R(0);
+  Quat<R> low{R(0), R(0), R(0), R(0)};
+  const Quat<R> A = su2c_staple<R, FIELD, MU, CG, meas>(a, parity, x, &low);
   const R k2 = qnorm2(A);
   constexpr bool phased = FIELD && MU == 1;
   R bc = R(1), bs = R(0);
   if (phased) load_phase<R>(a, x.c[0], bc, bs);
   const Quat<R> Bd{bc, R(0), R(0), -bs};  // B^+
-  Quat<R> ut_new;
+  Quat<R> u_new;
+  bool keep = false;  // the link stays as it is (it still gets the reunitarization)
   if (KIND == KIND_HB) {
     const R k = q_sqrt(k2);
     const R alpha = R(a.beta) * k;
     const Stream dir = make_stream(a.k0, a.k1, uint32_t(x.s), sweep, MU, 0, KIND_DIR);
+    Quat<R> ut_new;
     if (alpha == R(0)) {
       ut_new = su2_haar<R>(dir, 0u);
     } else {
@@ -86,23 +94,30 @@ __device__ __forceinline__ void su2c_update(const Ctx& a, int parity, int h, uin
       R delta;
       if (!kp_draw<R>(alpha, a.nhit, tries, delta)) {
         atomicAdd(a.exhausted, 1ull);
-        keep();
-        return;  // keep the link
+        keep = true;
+      } else {
+        ut_new = qmul(su2_with_delta<R>(delta, dir), qdag(qscale(A, R(1) / k)));
       }
-      ut_new = qmul(su2_with_delta<R>(delta, dir), qdag(qscale(A, R(1) / k)));
     }
+    if (keep) return R(0);  // heat-bath passes carry no reunitarization
+    u_new = phased ? qmul(ut_new, Bd) : ut_new;
   } else {
+    const Quat<R> u = P::template load<CG>(a.links, a.g, MU, parity, h);
     if (k2 == R(0)) {
-      keep();
-      return;
+      if (!reunit) return R(0);
+      u_new = u;
+    } else {
+      const Quat<R> Vd = qdag(qscale(A, R(1) / q_sqrt(k2)));
+      const Quat<R> ut = phased ? qmul(u, qdag(Bd)) : u;
+      const Quat<R> ut_new = qmul(qmul(Vd, qdag(ut)), Vd);
+      u_new = phased ? qmul(ut_new, Bd) : ut_new;
     }
-    const Quat<R> Vd = qdag(qscale(A, R(1) / q_sqrt(k2)));
-    Quat<R> ut = P::template load<CG>(a.links, a.g, MU, parity, h);
-    if (phased) ut = qmul(ut, qdag(Bd));
-    ut_new = qmul(qmul(Vd, qdag(ut)), Vd);
   }
-  const Quat<R> u_new = phased ? qmul(ut_new, Bd) : ut_new;
-  P::store(a.links, a.g, MU, parity, h, reunit ? su2_reunit_value<R>(u_new) : u_new);
+  if (reunit) u_new = su2_reunit_value<R>(u_new);
+  P::store(a.links, a.g, MU, parity, h, u_new);
+  if (!meas) return R(0);
+  const Quat<R> ut_final = phased ? qmul(u_new, qdag(Bd)) : u_new;
+  return qmul(ut_final, low).q0;  // (1/2) Re Tr(Ut low)
 }
 
 template <typename R, bool FIELD, int KIND, int MU>
@@ -110,6 +125,83 @@ __global__ void su2c_phase_kernel(const Ctx a, int parity) {
   const int h = blockIdx.x * blockDim.x + threadIdx.x;
   if (h >= a.g.Vh) return;
   su2c_update<R, FIELD, KIND, MU, false>(a, parity, h, KIND == KIND_HB ? *a.sweep : 0u);
+}
+
+// Sum of v over the block (any multiple of 32 threads) in a fixed order.
+__device__ __forceinline__ void su2c_block_sum(double v, double* out) {
+  __shared__ double sh[32];
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(0xffffffffu, v, off);
+  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = v;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double s = 0.0;
+    for (int w = 0; w < int(blockDim.x >> 5); ++w) s += sh[w];
+    *out = s;
+  }
+}
+
+// Last-pass phase (odd parity, MU >= 1) of a working sweep: update,
+// reunitarize and sum the plaquettes of the planes (MU, nu < MU).
+template <typename R, bool FIELD, int MU>
+__global__ void su2c_or_meas_kernel(const Ctx a, int parity) {
+  const int h = blockIdx.x * blockDim.x + threadIdx.x;
+  double v = 0.0;
+  if (h < a.g.Vh) v = double(su2c_update<R, FIELD, KIND_OR_MEAS, MU, false>(a, parity, h, 0u));
+  su2c_block_sum(v, a.partials + fused_plaq_offset(a.g, MU) + blockIdx.x);
+}
+
+// Final sums of an SU(2) working sweep's fused measurement.
+template <typename R>
+__global__ void __launch_bounds__(FINAL_THREADS) su2c_fused_final_kernel(const Ctx a, int grid) {
+  __shared__ double sh[4][FINAL_THREADS];
+  const int nl = meas_poly_blocks(a.g);
+  double s[4] = {0.0, 0.0, 0.0, 0.0};
+  for (int b = threadIdx.x; b < grid; b += FINAL_THREADS) {
+    s[0] += a.partials[fused_plaq_offset(a.g, 1) + b] + a.partials[fused_plaq_offset(a.g, 2) + b];
+    s[1] += a.partials[fused_plaq_offset(a.g, 3) + b];
+  }
+  for (int b = threadIdx.x; b < nl; b += FINAL_THREADS) {
+    s[2] += a.partials[2 * b];
+    s[3] += a.partials[2 * b + 1];
+  }
+#pragma unroll
+  for (int k = 0; k < 4; ++k) sh[k][threadIdx.x] = s[k];
+  __syncthreads();
+  for (int w = FINAL_THREADS / 2; w > 0; w >>= 1) {
+    if (int(threadIdx.x) < w) {
+#pragma unroll
+      for (int k = 0; k < 4; ++k) sh[k][threadIdx.x] += sh[k][threadIdx.x + w];
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    const double V = 2.0 * double(a.g.Vh);
+    const double V3 = double(a.g.Ns) * a.g.Ns * a.g.Ns;
+    a.meas_out[0] = (sh[0][0] + sh[1][0]) / (6.0 * V);
+    a.meas_out[1] = sh[0][0] / (3.0 * V);
+    a.meas_out[2] = sh[1][0] / (3.0 * V);
+    a.meas_out[3] = sh[2][0] / V3;
+    a.meas_out[4] = sh[3][0] / V3;
+  }
+}
+
+template <typename R>
+cudaError_t su2c_measure_fused_tail(const Ctx& a, int block, cudaStream_t st) {
+  const int nl = meas_poly_blocks(a.g);
+  measure_kernel<SU2Policy<R>, 0><<<nl, MEAS_THREADS, 0, st>>>(a, 0);  // Polyakov loop only
+  su2c_fused_final_kernel<R><<<1, FINAL_THREADS, 0, st>>>(a, int(grid_for(a.g.Vh, block)));
+  return cudaGetLastError();
+}
+
+template <typename R, bool FIELD>
+inline void su2c_launch_or_meas(const Ctx& a, int parity, int mu, int block, cudaStream_t st) {
+  const unsigned grid = grid_for(a.g.Vh, block);
+  switch (mu) {
+    case 1: su2c_or_meas_kernel<R, FIELD, 1><<<grid, block, 0, st>>>(a, parity); break;
+    case 2: su2c_or_meas_kernel<R, FIELD, 2><<<grid, block, 0, st>>>(a, parity); break;
+    default: su2c_or_meas_kernel<R, FIELD, 3><<<grid, block, 0, st>>>(a, parity); break;
+  }
 }
 
 template <typename R, bool FIELD, int KIND>
@@ -132,7 +224,10 @@ cudaError_t su2c_launch_phase(const Ctx& a, int kind, int parity, int mu, int bl
   } else if (kind == KIND_OR) {
     if (field) su2c_launch_kind<R, true, KIND_OR>(a, parity, mu, block, st);
     else su2c_launch_kind<R, false, KIND_OR>(a, parity, mu, block, st);
-  } else {  // KIND_OR_REUNIT (no fused measurement for SU(2))
+  } else if (kind == KIND_OR_MEAS && mu >= 1) {
+    if (field) su2c_launch_or_meas<R, true>(a, parity, mu, block, st);
+    else su2c_launch_or_meas<R, false>(a, parity, mu, block, st);
+  } else {
     if (field) su2c_launch_kind<R, true, KIND_OR_REUNIT>(a, parity, mu, block, st);
     else su2c_launch_kind<R, false, KIND_OR_REUNIT>(a, parity, mu, block, st);
   }
@@ -156,7 +251,13 @@ template <typename R>
 int su2c_max_phase_block() {
   const int m = std::min(std::min(su2c_limit_mu<R, false, KIND_HB>(), su2c_limit_mu<R, true, KIND_HB>()),
                          std::min(su2c_limit_mu<R, false, KIND_OR>(), su2c_limit_mu<R, true, KIND_OR>()));
-  return std::min(m, std::min(su2c_limit_mu<R, false, KIND_OR_REUNIT>(), su2c_limit_mu<R, true, KIND_OR_REUNIT>()));
+  cudaFuncAttributes f0{}, f1{};
+  const int meas = cudaFuncGetAttributes(&f0, su2c_or_meas_kernel<R, false, 3>) == cudaSuccess &&
+                           cudaFuncGetAttributes(&f1, su2c_or_meas_kernel<R, true, 1>) == cudaSuccess
+                       ? std::min(f0.maxThreadsPerBlock, f1.maxThreadsPerBlock)
+                       : 0;
+  return std::min(std::min(m, meas),
+                  std::min(su2c_limit_mu<R, false, KIND_OR_REUNIT>(), su2c_limit_mu<R, true, KIND_OR_REUNIT>()));
 }
 
 template <typename R>
@@ -172,7 +273,7 @@ PolicyOps su2c_ops(int precision) {
                    &launch_to_canonical<P>,
                    &launch_from_canonical<P>,
                    &launch_set_frozen<P>,
-                   nullptr,
+                   &su2c_measure_fused_tail<R>,
                    &su2c_max_phase_block<R>};
 }
 
