@@ -392,6 +392,37 @@ def run_on_model(q, stream):
     return out
 
 
+def run_split(q, stream, w):
+    """The working-sweep workload on lattices divided along t between device
+    memory and host memory (the remedy for lattices larger than the device
+    memory): link updates/s with the last 4 and the last 8 of the 16 t-slices
+    in host memory, read and written by the GPU over the CPU-GPU link."""
+    import torch
+    out = {"workload": w.name, "unit": UNIT}
+    for nt_dev in (w.Nt * 3 // 4, w.Nt // 2):
+        try:
+            lat = q.Lattice(w.group, w.Ns, w.Nt, w.beta, w.flux, q.QCD_FP32_COMPRESSED, q.QCD_HOT, w.seed, stream,
+                            nt_device=nt_dev)
+        except q.QcdError as e:
+            out["nt_device_%d" % nt_dev] = {"unavailable": str(e)}
+            continue
+        dev_b, host_b, got = q.qcd_get_residency(lat.h)
+        q.qcd_working_sweep(lat.h, 1, w.n_or, w.seed)
+        torch.cuda.synchronize()
+        n = 2
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(n):
+            q.qcd_working_sweep(lat.h, 1, w.n_or, w.seed)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / n
+        out["nt_device_%d" % got] = {"value": (1 + w.n_or) * 4 * w.volume / (ms / 1e3), "ms_per_step": ms,
+                                     "device_link_bytes": dev_b, "host_link_bytes": host_b}
+        lat.close()
+    return out
+
+
 def main():
     args = parse()
     w = workloads.SU3_64x16
@@ -550,6 +581,7 @@ def main():
         extras["batched"] = run_batched(q, stream, world, rank, dist, workloads.batch_scan().sweeps)
         extras["o4_model"] = run_on_model(q, stream)
         extras["paper_lattices"] = run_paper_lattices(q, stream)
+        extras["split_residency"] = run_split(q, stream, w)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:

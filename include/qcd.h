@@ -115,6 +115,35 @@ int qcd_lattice_create_ex(qcd_lattice **out, int group, int Ns, int Nt,
                           double beta, int flux, int flux8, int field_mode,
                           int precision, int start, uint64_t seed,
                           void *stream);
+/* A lattice divided into two parts along t (Sect. "Multi-GPU Mode and
+ * Distributed Simulations": dividing the lattice is also the remedy when the
+ * device memory is too small).  Arguments as for qcd_lattice_create_ex, plus
+ *   nt_device   t-slices 0 .. nt_device-1 of every link array are placed in
+ *               device memory and the rest in pinned host memory of the NUMA
+ *               node next to the GPU; 0 <= nt_device <= Nt, else
+ *               QCD_ERR_INVALID_ARG.  The device part is rounded up to the
+ *               mapping granule (2 MB on GB300): qcd_get_residency reports
+ *               what was placed.
+ * Both parts sit behind one virtual address range, so every kernel, sweep,
+ * measurement and copy behaves exactly as on a device-resident lattice and
+ * gives bit-identical results; the host part is read and written by the GPU
+ * over the CPU-GPU link, at that link's bandwidth.  Each link array is padded
+ * to a whole number of granules.  Split lattices skip the launch-shape
+ * autotuner (128 threads per block unless a tuned shape for the same
+ * lattice is cached or qcd_set_block sets one).  qcd_get_links / qcd_set_links
+ * (and the checkpoint calls built on them) stage the canonical FP64 copy in
+ * device memory, so they need room for it there.  QCD_ERR_NOT_SUPPORTED when
+ * the device cannot map host-NUMA memory; QCD_ERR_OOM when either part cannot
+ * be allocated. */
+int qcd_lattice_create_split(qcd_lattice **out, int group, int Ns, int Nt,
+                             double beta, int flux, int flux8, int field_mode,
+                             int precision, int start, uint64_t seed,
+                             void *stream, int nt_device);
+/* Bytes of link storage in device and in host memory (padding included) and
+ * the number of leading t-slices wholly in device memory (Nt for an ordinary
+ * lattice). */
+int qcd_get_residency(qcd_lattice *lat, size_t *device_bytes,
+                      size_t *host_bytes, int *nt_device);
 int qcd_lattice_destroy(qcd_lattice *lat);
 /* The field mode the lattice was created with. */
 int qcd_get_field_mode(qcd_lattice *lat, int *field_mode);

@@ -39,6 +39,8 @@ _P = ctypes.POINTER
 SIGNATURES = {
     "qcd_lattice_create": (_i, [_P(_vp), _i, _i, _i, _d, _i, _i, _i, _u64, _vp]),
     "qcd_lattice_create_ex": (_i, [_P(_vp), _i, _i, _i, _d, _i, _i, _i, _i, _i, _u64, _vp]),
+    "qcd_lattice_create_split": (_i, [_P(_vp), _i, _i, _i, _d, _i, _i, _i, _i, _i, _u64, _vp, _i]),
+    "qcd_get_residency": (_i, [_vp, _P(_sz), _P(_sz), _P(_i)]),
     "qcd_lattice_destroy": (_i, [_vp]),
     "qcd_get_field_mode": (_i, [_vp, _P(_i)]),
     "qcd_set_nhit": (_i, [_vp, _i]),
@@ -155,6 +157,22 @@ def qcd_lattice_create_ex(group, Ns, Nt, beta, flux=0, flux8=0, field_mode=QCD_F
     _check(lib().qcd_lattice_create_ex(ctypes.byref(h), group, Ns, Nt, beta, flux, flux8, field_mode,
                                        precision, start, seed, _stream_handle(stream)))
     return h
+
+
+def qcd_lattice_create_split(group, Ns, Nt, beta, flux=0, flux8=0, field_mode=QCD_FIELD_LINKS,
+                             precision=QCD_FP32_COMPRESSED, start=QCD_HOT, seed=1, stream=None,
+                             nt_device=0) -> ctypes.c_void_p:
+    h = ctypes.c_void_p()
+    _check(lib().qcd_lattice_create_split(ctypes.byref(h), group, Ns, Nt, beta, flux, flux8, field_mode,
+                                          precision, start, seed, _stream_handle(stream), nt_device))
+    return h
+
+
+def qcd_get_residency(h):
+    """(device bytes, host bytes, leading t-slices wholly in device memory)."""
+    d, hb, nt = ctypes.c_size_t(), ctypes.c_size_t(), ctypes.c_int()
+    _check(lib().qcd_get_residency(h, ctypes.byref(d), ctypes.byref(hb), ctypes.byref(nt)))
+    return d.value, hb.value, nt.value
 
 
 def qcd_get_field_mode(h) -> int:
@@ -411,13 +429,20 @@ class Lattice:
     """Owning wrapper around one ``qcd_lattice`` handle."""
 
     def __init__(self, group, Ns, Nt, beta, flux=0, precision=QCD_FP32_COMPRESSED,
-                 start=QCD_HOT, seed=1, stream=None, nhit=10, field_mode=QCD_FIELD_LINKS, flux8=0):
+                 start=QCD_HOT, seed=1, stream=None, nhit=10, field_mode=QCD_FIELD_LINKS, flux8=0,
+                 nt_device=None):
+        """nt_device: None for a device-resident lattice, else the number of
+        leading t-slices kept in device memory (the rest in host memory)."""
         self.group, self.Ns, self.Nt = group, Ns, Nt
         self.V = Ns ** 3 * Nt
         self.beta, self.flux, self.precision, self.seed = beta, flux, precision, seed
         self.field_mode, self.flux8 = field_mode, flux8
-        self.h = qcd_lattice_create_ex(group, Ns, Nt, beta, flux, flux8, field_mode, precision, start,
-                                       seed, stream)
+        if nt_device is None:
+            self.h = qcd_lattice_create_ex(group, Ns, Nt, beta, flux, flux8, field_mode, precision, start,
+                                           seed, stream)
+        else:
+            self.h = qcd_lattice_create_split(group, Ns, Nt, beta, flux, flux8, field_mode, precision, start,
+                                              seed, stream, nt_device)
         if nhit != 10:
             qcd_set_nhit(self.h, nhit)
 

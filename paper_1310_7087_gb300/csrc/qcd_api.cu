@@ -111,6 +111,8 @@ struct qcd_lattice {
   qcd::GeomH g{};
   void* links = nullptr;
   size_t link_bytes = 0;
+  qcd::SplitLinks* split = nullptr;  // non-null: links divided between device and host memory
+  size_t split_device_bytes = 0;     // device-resident bytes of each link array
   unsigned char* d_small = nullptr;  // sweep counter, exhaustion counter, results
   uint32_t* d_sweep = nullptr;
   unsigned long long* d_exhausted = nullptr;
@@ -367,7 +369,7 @@ int autotune(qcd_lattice* L) {
     }
   }
   const char* env = getenv("QCD_AUTOTUNE");
-  if (env && env[0] == '0') {
+  if ((env && env[0] == '0') || L->split) {  // a split lattice may not fit a device scratch copy
     L->block = 128;
     return QCD_OK;
   }
@@ -439,8 +441,41 @@ int qcd_lattice_create(qcd_lattice** out, int group, int Ns, int Nt, double beta
   return qcd_lattice_create_ex(out, group, Ns, Nt, beta, flux, 0, QCD_FIELD_LINKS, precision, start, seed, stream);
 }
 
+namespace {
+int create_lattice(qcd_lattice** out, int group, int Ns, int Nt, double beta, int flux, int flux8, int field_mode,
+                   int precision, int start, uint64_t seed, void* stream, int nt_device);
+}
+
 int qcd_lattice_create_ex(qcd_lattice** out, int group, int Ns, int Nt, double beta, int flux, int flux8,
                           int field_mode, int precision, int start, uint64_t seed, void* stream) {
+  return create_lattice(out, group, Ns, Nt, beta, flux, flux8, field_mode, precision, start, seed, stream, -1);
+}
+
+int qcd_lattice_create_split(qcd_lattice** out, int group, int Ns, int Nt, double beta, int flux, int flux8,
+                             int field_mode, int precision, int start, uint64_t seed, void* stream, int nt_device) {
+  if (nt_device < 0 || nt_device > Nt)
+    return set_error(QCD_ERR_INVALID_ARG, "nt_device must be in [0, Nt], got %d", nt_device);
+  return create_lattice(out, group, Ns, Nt, beta, flux, flux8, field_mode, precision, start, seed, stream,
+                        nt_device);
+}
+
+int qcd_get_residency(qcd_lattice* L, size_t* device_bytes, size_t* host_bytes, int* nt_device) {
+  if (int rc = check(L)) return rc;
+  if (!device_bytes || !host_bytes || !nt_device) return set_error(QCD_ERR_INVALID_ARG, "null output pointer");
+  const size_t n_arrays = size_t(L->ops->comps) * 8;
+  const size_t array_bytes = L->link_bytes / n_arrays;
+  const size_t dev = L->split ? L->split_device_bytes : array_bytes;
+  *device_bytes = n_arrays * dev;
+  *host_bytes = n_arrays * (array_bytes - dev);
+  // t-slices wholly in device memory: each t-slice of an array is Ns^3/2 vectors of 16 bytes
+  const size_t slice = size_t(L->Ns) * L->Ns * L->Ns / 2 * 16;
+  *nt_device = int(std::min<size_t>(size_t(L->Nt), dev / slice));
+  return QCD_OK;
+}
+
+namespace {
+int create_lattice(qcd_lattice** out, int group, int Ns, int Nt, double beta, int flux, int flux8, int field_mode,
+                   int precision, int start, uint64_t seed, void* stream, int nt_device) {
   if (!out) return set_error(QCD_ERR_INVALID_ARG, "out is null");
   *out = nullptr;
   if (group == 2 && flux8 != 0) return set_error(QCD_ERR_INVALID_ARG, "the lambda8 flux needs SU(3)");
@@ -480,10 +515,31 @@ int qcd_lattice_create_ex(qcd_lattice** out, int group, int Ns, int Nt, double b
   };
   cudaError_t e = cudaGetDevice(&L->device);
   if (e != cudaSuccess) return fail(set_error(QCD_ERR_CUDA, "cudaGetDevice: %s", cudaGetErrorString(e)));
+  if (nt_device >= 0) {
+    // Every link array padded to a whole number of mapping granules; its
+    // first t-slices (rounded up to a granule) in device memory, the rest in
+    // host memory.
+    size_t gran = 0;
+    const int node = qcd::split_host_node(L->device, &gran);
+    if (node < 0)
+      return fail(set_error(QCD_ERR_NOT_SUPPORTED, "this device cannot map host-NUMA memory into its address space"));
+    const size_t vecs = gran / 16;
+    L->g.plane = int64_t((size_t(L->g.Vh) + vecs - 1) / vecs * vecs);
+    const size_t n_arrays = size_t(L->ops->comps) * 8, array_bytes = size_t(L->g.plane) * 16;
+    L->link_bytes = n_arrays * array_bytes;
+    const size_t want = size_t(nt_device) * (size_t(Ns) * Ns * Ns / 2) * 16;
+    L->split_device_bytes = std::min(array_bytes, (want + gran - 1) / gran * gran);
+    char why[256] = {0};
+    if (int rc = qcd::split_alloc(L->device, node, gran, n_arrays, array_bytes, L->split_device_bytes, &L->split,
+                                  &L->links, why, sizeof why))
+      return fail(set_error(rc, "%s", why));
+  } else if (cudaMalloc(&L->links, L->link_bytes) != cudaSuccess) {
+    cudaGetLastError();
+    return fail(set_error(QCD_ERR_OOM, "device allocation of %zu bytes of links failed", L->link_bytes));
+  }
   const size_t n_part = std::max(qcd::measure_partials(L->g), qcd::fused_partials(L->g));
   const size_t small_bytes = 256;
-  if (cudaMalloc(&L->links, L->link_bytes) != cudaSuccess ||
-      cudaMalloc(reinterpret_cast<void**>(&L->d_small), small_bytes) != cudaSuccess ||
+  if (cudaMalloc(reinterpret_cast<void**>(&L->d_small), small_bytes) != cudaSuccess ||
       cudaMalloc(reinterpret_cast<void**>(&L->d_partials), n_part * sizeof(double)) != cudaSuccess ||
       cudaMalloc(reinterpret_cast<void**>(&L->d_phase64), 4 * Ns * sizeof(double2)) != cudaSuccess ||
       cudaMalloc(reinterpret_cast<void**>(&L->d_phase32), 4 * Ns * sizeof(float2)) != cudaSuccess) {
@@ -507,6 +563,7 @@ int qcd_lattice_create_ex(qcd_lattice** out, int group, int Ns, int Nt, double b
   *out = L;
   return QCD_OK;
 }
+}  // namespace
 
 int qcd_get_field_mode(qcd_lattice* L, int* field_mode) {
   if (int rc = check(L)) return rc;
@@ -522,7 +579,8 @@ int qcd_lattice_destroy(qcd_lattice* L) {
   drop_graphs(L);
   for (cudaEvent_t e : L->meas_ev)
     if (e) cudaEventDestroy(e);
-  cudaFree(L->links);
+  if (L->split) qcd::split_free(L->split);
+  else cudaFree(L->links);
   cudaFree(L->d_small);
   cudaFree(L->d_partials);
   cudaFree(L->d_phase64);
