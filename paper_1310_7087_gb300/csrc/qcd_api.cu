@@ -5,6 +5,7 @@
 // in the kernels of su{2,3}_f{32,64}.cu.
 #include "qcd.h"
 #include "qcd_internal.h"
+#include "qcd_split.h"
 
 #include <cstdarg>
 #include <cstdio>

@@ -98,17 +98,6 @@ inline int su3_field_level(const Ctx& a) { return !phases_on_links(a) ? 0 : (a.f
 // Record the message returned by qcd_last_error() on this thread; returns code.
 int set_last_error(int code, const char* msg);
 
-// Link storage divided along t into a device part and a host part behind one
-// virtual address range (qcd_split.cu).  split_host_node returns the host NUMA
-// node next to `device` and the mapping granularity, or -1 when the device
-// cannot map host memory this way.  split_alloc returns a QCD_* code and, on
-// failure, a message in why.
-struct SplitLinks;
-int split_host_node(int device, size_t* granularity);
-int split_alloc(int device, int node, size_t granularity, size_t n_arrays, size_t array_bytes, size_t device_bytes,
-                SplitLinks** out, void** base, char* why, size_t why_len);
-void split_free(SplitLinks* s);
-
 extern const PolicyOps kOpsSU2F64;
 extern const PolicyOps kOpsSU2F32;
 extern const PolicyOps kOpsSU3F64;

@@ -14,7 +14,7 @@
 // The driver entry points come from cudaGetDriverEntryPointByVersion, so the
 // library has no link-time dependency on libcuda.
 #include "qcd.h"
-#include "qcd_internal.h"
+#include "qcd_split.h"
 
 #include <cuda.h>
 
