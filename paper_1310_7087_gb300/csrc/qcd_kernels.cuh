@@ -420,6 +420,11 @@ __device__ __forceinline__ double rsqrt1p_minus1(double e) {
   return e * fma(e, fma(e, -0.3125, 0.375), -0.5);
 }
 
+// 1/sqrt(n) - 1 in FP64 for a norm far from 1 (rare), out of line so that the
+// hot code of the callers stays small (SU(2): batched scan 0.581 -> 0.575
+// ms/sweep; the same for the SU(3) rows measured 1 % slower and is not done).
+static __device__ __noinline__ float rsqrt_minus1_far(double n) { return float(rsqrt_fp64(n) - 1.0); }
+
 template <typename R>
 __device__ __forceinline__ Quat<R> su2_reunit_value(const Quat<R>& u) {
   if constexpr (sizeof(R) == 4) {
@@ -430,8 +435,7 @@ __device__ __forceinline__ Quat<R> su2_reunit_value(const Quat<R>& u) {
     n.add(u.q2, u.q2);
     n.add(u.q3, u.q3);
     const float e = dot2_excess(n);
-    const float d = fabsf(e) <= REUNIT_SERIES_MAX ? float(rsqrt1p_minus1(double(e)))
-                                                  : float(rsqrt_fp64(n.value()) - 1.0);
+    const float d = fabsf(e) <= REUNIT_SERIES_MAX ? float(rsqrt1p_minus1(double(e))) : rsqrt_minus1_far(n.value());
     return Quat<R>{scale1p(u.q0, d), scale1p(u.q1, d), scale1p(u.q2, d), scale1p(u.q3, d)};
   } else {
     const double q0 = u.q0, q1 = u.q1, q2 = u.q2, q3 = u.q3;

@@ -264,6 +264,21 @@ __device__ __forceinline__ M3<float> su3c_staple(const Ctx& a, int p, const LexS
   return A;
 }
 
+// One Kennedy-Pendleton subgroup step of the FP32 heat-bath: the rotation
+// R = X V^+ for the normalized block wn = V, or q0 = 2 when every try failed.
+// Not inlined: the three subgroups share one copy of the sampling code.
+static __device__ __noinline__ Quat<float> su3c_kp_rotation(float alpha, int nhit, Stream tries, Stream dir,
+                                                            Quat<float> wn) {
+  float delta;
+  if (!kp_draw<float>(alpha, nhit, tries, delta)) return {2.f, 0.f, 0.f, 0.f};
+  const Quat<float> X = su2_with_delta<float>(delta, dir);
+  return qmul(X, qdag(wn));
+}
+
+// The alpha = 0 case (Haar-random rotation), out of line: it is never taken at
+// beta > 0 and would otherwise sit in the hot code.
+static __device__ __noinline__ Quat<float> su3c_haar_rotation(Stream dir) { return su2_haar<float>(dir, 0u); }
+
 // Heat-bath or overrelaxation of U_MU(x) given its staple sum A.
 // Returns the link as stored (rows 0-1; row 2 not kept up to date).
 template <int FIELD, int KIND, int MU>
@@ -303,16 +318,14 @@ __device__ __forceinline__ M3<float> su3c_update(const Ctx& a, int parity, int h
       const float alpha = float(2.0 / 3.0) * float(a.beta) * k;
       const Stream dir = make_stream(a.k0, a.k1, uint32_t(x.s), sweep, MU, sub, KIND_DIR);
       if (alpha == 0.f) {
-        r = su2_haar<float>(dir, 0u);
+        r = su3c_haar_rotation(dir);
       } else {
         const Stream tries = make_stream(a.k0, a.k1, uint32_t(x.s), sweep, MU, sub, KIND_TRY);
-        float delta;
-        if (!kp_draw<float>(alpha, a.nhit, tries, delta)) {
+        r = su3c_kp_rotation(alpha, a.nhit, tries, dir, qscale(w, rk));
+        if (r.q0 > 1.5f) {
           ++exhausted;
           continue;
         }
-        const Quat<float> X = su2_with_delta<float>(delta, dir);
-        r = qmul(X, qdag(qscale(w, rk)));
       }
     } else {
       if (n2 == 0.f) continue;
