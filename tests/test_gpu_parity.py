@@ -386,6 +386,21 @@ def test_working_sweep_equals_sweep_then_measure(q, group, precision, flux, flux
     b.close()
 
 
+@pytest.mark.parametrize("Ns,Nt", [(4, 2), (6, 6), (4, 8), (8, 16), (6, 10)])
+def test_fused_polyakov_any_nt(q, Ns, Nt):
+    """The fused Polyakov loop (its own kernel, products by rows 0-1 with row 2
+    rebuilt) gives the measurement of qcd_measure at every time extent,
+    including the partly unrolled t-loop's remainders."""
+    a = q.Lattice(3, Ns, Nt, 5.8, 1, FP32_COMPRESSED, HOT, 5)
+    b = q.Lattice(3, Ns, Nt, 5.8, 1, FP32_COMPRESSED, HOT, 5)
+    got = q.qcd_working_sweep(a.h, 1, 2, 5)
+    b.sweep(1, 2, 5)
+    (p, l) = b.measure()
+    assert np.abs(np.array(got) - np.array(list(p) + list(l))).max() <= 1e-6, (got, p, l)
+    a.close()
+    b.close()
+
+
 def test_working_sweep_matches_oracle_measure(q):
     """Fused measurement on a 16^3 x 4 FP32 lattice against the oracle's
     measurement of the same configuration."""
