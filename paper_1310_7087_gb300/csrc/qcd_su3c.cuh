@@ -356,8 +356,21 @@ __device__ __forceinline__ void block_sum_any(double v, double* out) {
   }
 }
 
+// Register caps (64^3x16, per launch): overrelaxation QCD_SU3_PHASE_MAXNREG
+// (96); heat-bath 128 (0.2291 ms; 80 / 96 / 112 / 160 / 200: 0.2581 / 0.2359 /
+// 0.2392 / 0.2660 / 0.2640); the reunitarizing overrelaxation of the last
+// pass 128 (its group 0.1921 -> 0.1908 ms per launch against 96; 112: 0.1940).
+#ifndef QCD_SU3_HB_MAXNREG
+#define QCD_SU3_HB_MAXNREG 128
+#endif
+#ifndef QCD_SU3_REUNIT_MAXNREG
+#define QCD_SU3_REUNIT_MAXNREG 128
+#endif
+
 template <int FIELD, int KIND, int MU>
-__global__ void __maxnreg__(QCD_SU3_PHASE_MAXNREG) su3c_phase_kernel(const Ctx a, int parity) {
+__global__ void __maxnreg__(KIND == KIND_HB          ? QCD_SU3_HB_MAXNREG
+                            : KIND == KIND_OR_REUNIT ? QCD_SU3_REUNIT_MAXNREG
+                                                     : QCD_SU3_PHASE_MAXNREG) su3c_phase_kernel(const Ctx a, int parity) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= a.g.Vh) return;
   const LexSite x = lex_site_ytz(a.g, parity, i);
