@@ -41,6 +41,14 @@ UNIT = "link updates/s"
 # same direction, V/2 read + V/2 written, for V/2 updates per phase).
 LINK_BYTES = {(3, 1): 48, (3, 0): 144, (2, 1): 16, (2, 0): 32}
 TRANSFERS_PER_UPDATE = 9
+# FP64 flops of one SU(3) overrelaxation update in the FP64 kernel (FMA = 2):
+# staple 12 full 3x3 complex products (324 complex multiply-adds), W = U A
+# (27), the three subgroup rotations of U and the first two of W (60), at 8
+# flops each = 3,288, plus ~150 for the projections, norms and quaternion
+# squares.  FP64 peak: the nominal 1.25 TFLOP/s of GB300 (152 SMs x 2 FP64
+# FMA per clock x 2 flops x 2.07 GHz = 1.26e12); no measured FP64 peak.
+FP64_OR_FLOPS = 3438
+FP64_PEAK_TFLOPS = 1.25
 
 
 def parse():
@@ -576,6 +584,13 @@ def main():
                                 "kernel_ms_per_step": {n: round(m / n64, 3) for n, m in zip(names, pm)},
                                 "fp32_speedup": (lu_per_step * args.steps / (t_ms / 1e3)) /
                                                 (lu_per_step / (ms64 / 1e3))}
+        if pn[1]:
+            or_ms = pm[1] / pn[1]
+            tf = FP64_OR_FLOPS * (w.volume // 2) / (or_ms / 1e3) / 1e12
+            extras["fp64_plain"]["roofline"] = {
+                "bound": "alu", "kernel": "overrelax_phase", "unit": "TFLOP/s", "achieved": tf,
+                "peak": FP64_PEAK_TFLOPS, "frac": tf / FP64_PEAK_TFLOPS, "flops_per_update": FP64_OR_FLOPS,
+                "avg_launch_ms": or_ms, "peak_source": "nominal GB300 FP64 (no measured FP64 peak)"}
         lat64.close()
 
         extras["batched"] = run_batched(q, stream, world, rank, dist, workloads.batch_scan().sweeps)

@@ -454,6 +454,8 @@ int qcd_lattice_create_ex(qcd_lattice** out, int group, int Ns, int Nt, double b
 
 int qcd_lattice_create_split(qcd_lattice** out, int group, int Ns, int Nt, double beta, int flux, int flux8,
                              int field_mode, int precision, int start, uint64_t seed, void* stream, int nt_device) {
+  if (!out) return set_error(QCD_ERR_INVALID_ARG, "out is null");
+  *out = nullptr;
   if (nt_device < 0 || nt_device > Nt)
     return set_error(QCD_ERR_INVALID_ARG, "nt_device must be in [0, Nt], got %d", nt_device);
   return create_lattice(out, group, Ns, Nt, beta, flux, flux8, field_mode, precision, start, seed, stream,

@@ -60,3 +60,18 @@ def test_no_cpu_fallback_without_library(tmp_path, monkeypatch):
     monkeypatch.setattr(q, "_lib", None)
     with pytest.raises(RuntimeError, match="no CPU fallback"):
         q.lib()
+
+
+def test_split_lattice_argument_checks_need_no_gpu(built_lib):
+    """qcd_lattice_create_split rejects nt_device outside [0, Nt] before any
+    CUDA call, leaving the handle null, and says why."""
+    import paper_1310_7087_gb300 as q
+    q._lib = None  # bind the freshly built library
+    lib = q.lib()
+    for nt_device in (-1, 5):
+        h = ctypes.c_void_p(1234)
+        rc = lib.qcd_lattice_create_split(ctypes.byref(h), 3, 4, 4, 5.7, 0, 0, q.QCD_FIELD_LINKS,
+                                          q.QCD_FP32_COMPRESSED, q.QCD_HOT, 1, None, nt_device)
+        assert rc == q.QCD_ERR_INVALID_ARG
+        assert not h.value
+        assert b"nt_device" in lib.qcd_last_error()
