@@ -275,18 +275,21 @@ __device__ __forceinline__ bool kp_draw(R alpha, int nhit, const Stream& st, R& 
 // errors (about 2^-21) move delta by less than 1e-7 / alpha, below the FP32
 // resolution of a0 = 1 - delta; cos^2 is taken at 2 pi (u - 1/2), inside the
 // fast cosine's accurate range, which leaves cos^2 unchanged.
+// One FP32 try on the four uniforms of its block.
+__device__ __forceinline__ bool kp_try_f32(const float u[4], float inv_alpha, float& delta) {
+  const float c = __cosf(6.283185307179586f * (u[2] - 0.5f));
+  const float d = (-__logf(u[1]) - __logf(u[0]) * c * c) * inv_alpha;
+  delta = d;
+  return u[3] * u[3] <= 1.f - 0.5f * d;
+}
+
 template <>
 __device__ __forceinline__ bool kp_draw<float>(float alpha, int nhit, const Stream& st, float& delta) {
   const float inv_alpha = __fdividef(1.f, alpha);
   for (int t = 0; t < nhit; ++t) {
     float u[4];
     st.uniforms<float>(uint32_t(t), u);
-    const float c = __cosf(6.283185307179586f * (u[2] - 0.5f));
-    const float d = (-__logf(u[1]) - __logf(u[0]) * c * c) * inv_alpha;
-    if (u[3] * u[3] <= 1.f - 0.5f * d) {
-      delta = d;
-      return true;
-    }
+    if (kp_try_f32(u, inv_alpha, delta)) return true;
   }
   return false;
 }
@@ -310,10 +313,8 @@ __device__ __forceinline__ Quat<R> su2_with_delta(R delta, const Stream& dir) {
 
 // FP32: the azimuth's sine and cosine from the hardware pair at
 // 2 pi (u - 1/2) (both change sign against 2 pi u), approximate square roots.
-template <>
-__device__ __forceinline__ Quat<float> su2_with_delta<float>(float delta, const Stream& dir) {
-  float u[4];
-  dir.uniforms<float>(0u, u);
+// ... from the direction block's uniforms u.
+__device__ __forceinline__ Quat<float> su2_with_delta_u(float delta, const float u[4]) {
   // square roots as x rsqrt(x): both arguments are positive (u0 in (0, 1),
   // delta > 0 since -ln u > 0 for every uniform)
   const float ct = 2.f * u[0] - 1.f;
@@ -324,6 +325,13 @@ __device__ __forceinline__ Quat<float> su2_with_delta<float>(float delta, const 
   const float e = delta * (2.f - delta);
   const float r = e * rsqrtf(e);
   return {1.f - delta, -r * st * cp, -r * st * sp, r * ct};
+}
+
+template <>
+__device__ __forceinline__ Quat<float> su2_with_delta<float>(float delta, const Stream& dir) {
+  float u[4];
+  dir.uniforms<float>(0u, u);
+  return su2_with_delta_u(delta, u);
 }
 
 // Haar-random unit quaternion (Shoemake) from one block.
