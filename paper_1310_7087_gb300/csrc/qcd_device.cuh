@@ -334,6 +334,24 @@ __device__ __forceinline__ Quat<float> su2_with_delta<float>(float delta, const 
   return su2_with_delta_u(delta, u);
 }
 
+// FP32 draw of the unit quaternion X = (1 - delta, direction): the direction
+// block does not depend on the tries, so it is drawn together with try 0 (two
+// independent Philox chains interleave).  False when all nhit tries fail.
+__device__ __forceinline__ bool kp_draw_dir_f32(float alpha, int nhit, const Stream& tries, const Stream& dir,
+                                                Quat<float>& X) {
+  const float inv_alpha = __fdividef(1.f, alpha);
+  float u[4], v[4], delta;
+  tries.uniforms<float>(0u, u);
+  dir.uniforms<float>(0u, v);
+  bool ok = kp_try_f32(u, inv_alpha, delta);
+  for (int t = 1; !ok && t < nhit; ++t) {
+    tries.uniforms<float>(uint32_t(t), u);
+    ok = kp_try_f32(u, inv_alpha, delta);
+  }
+  if (ok) X = su2_with_delta_u(delta, v);
+  return ok;
+}
+
 // Haar-random unit quaternion (Shoemake) from one block.
 template <typename R>
 __device__ __forceinline__ Quat<R> su2_haar(const Stream& st, uint32_t block) {

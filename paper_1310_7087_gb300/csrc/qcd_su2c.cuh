@@ -91,12 +91,20 @@ __device__ __forceinline__ R su2c_update(const Ctx& a, int parity, int h, uint32
       ut_new = su2_haar<R>(dir, 0u);
     } else {
       const Stream tries = make_stream(a.k0, a.k1, uint32_t(x.s), sweep, MU, 0, KIND_TRY);
-      R delta;
-      if (!kp_draw<R>(alpha, a.nhit, tries, delta)) {
+      Quat<R> X;
+      bool ok;
+      if constexpr (sizeof(R) == 4) {
+        ok = kp_draw_dir_f32(alpha, a.nhit, tries, dir, X);
+      } else {
+        R delta;
+        ok = kp_draw<R>(alpha, a.nhit, tries, delta);
+        if (ok) X = su2_with_delta<R>(delta, dir);
+      }
+      if (!ok) {
         atomicAdd(a.exhausted, 1ull);
         keep = true;
       } else {
-        ut_new = qmul(su2_with_delta<R>(delta, dir), qdag(qscale(A, R(1) / k)));
+        ut_new = qmul(X, qdag(qscale(A, R(1) / k)));
       }
     }
     if (keep) return R(0);  // heat-bath passes carry no reunitarization

@@ -267,21 +267,11 @@ __device__ __forceinline__ M3<float> su3c_staple(const Ctx& a, int p, const LexS
 // One Kennedy-Pendleton subgroup step of the FP32 heat-bath: the rotation
 // R = X V^+ for the normalized block wn = V, or q0 = 2 when every try failed.
 // Not inlined: the three subgroups share one copy of the sampling code.
-// The direction block does not depend on the tries, so it is drawn together
-// with try 0: two independent Philox chains interleave.
 static __device__ __noinline__ Quat<float> su3c_kp_rotation(float alpha, int nhit, Stream tries, Stream dir,
                                                             Quat<float> wn) {
-  const float inv_alpha = __fdividef(1.f, alpha);
-  float u[4], v[4], delta;
-  tries.uniforms<float>(0u, u);
-  dir.uniforms<float>(0u, v);
-  bool ok = kp_try_f32(u, inv_alpha, delta);
-  for (int t = 1; !ok && t < nhit; ++t) {
-    tries.uniforms<float>(uint32_t(t), u);
-    ok = kp_try_f32(u, inv_alpha, delta);
-  }
-  if (!ok) return {2.f, 0.f, 0.f, 0.f};
-  return qmul(su2_with_delta_u(delta, v), qdag(wn));
+  Quat<float> X;
+  if (!kp_draw_dir_f32(alpha, nhit, tries, dir, X)) return {2.f, 0.f, 0.f, 0.f};
+  return qmul(X, qdag(wn));
 }
 
 // The alpha = 0 case (Haar-random rotation), out of line: it is never taken at
