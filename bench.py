@@ -96,16 +96,17 @@ def kernel_source_sha():
     return h.hexdigest()[:16]
 
 
-def ncu_traffic(kernel_kind):
+def ncu_traffic(kernel_kind, workload):
     """DRAM bytes per launch of the dominant kernel from the committed ncu
-    summary, if it was taken on the current kernel sources; else None."""
+    summary, if it was taken on the current kernel sources and on this
+    workload; else None."""
     path = os.path.join(ROOT, "profiles", "ncu_traffic.json")
     if not os.path.exists(path):
         return None
     with open(path) as f:
         d = json.load(f)
     e = d.get(kernel_kind)
-    if not e or e.get("source_sha") != kernel_source_sha():
+    if not e or e.get("source_sha") != kernel_source_sha() or e.get("config") != workload:
         return None
     return e.get("dram_bytes_per_launch")
 
@@ -507,7 +508,7 @@ def main():
     peak, peak_src = load_peaks()
     achieved = alg_bytes / (per_launch_ms / 1e3) / 1e9
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                "traffic": ncu_traffic(names[dom]), "kernel": names[dom],
+                "traffic": ncu_traffic(names[dom], w.name), "kernel": names[dom],
                 "peak_source": "%s (MEASURED_PEAKS.json hbm_gbs)" % peak_src if peak_src == "measured"
                 else "fallback 6.8 TB/s",
                 "alg_bytes_per_launch": alg_bytes, "avg_launch_ms": per_launch_ms,
