@@ -576,7 +576,7 @@ int qcd_batch_create(qcd_batch** out, int n, int group, const int* Ns, const int
   for (int i = 0; i < n && e == cudaSuccess; ++i) {
     qcd::Ctx a{};
     a.links = B->links + B->lat[i].link_off;
-    a.g = {B->lat[i].Ns, B->lat[i].Nt, B->lat[i].Vh, B->lat[i].plane};
+    a.g = {B->lat[i].Ns, B->lat[i].Nt, B->lat[i].Vh, 0, B->lat[i].plane};
     a.k0 = uint32_t(seed) ^ B->lat[i].kxor;
     a.k1 = uint32_t(seed >> 32);
     e = B->ops->start(a, start, B->stream);
@@ -698,7 +698,7 @@ int qcd_batch_get_links(qcd_batch* B, int index, double* host_out) {
   BATCH_CUDA(cudaMalloc(reinterpret_cast<void**>(&tmp), bytes));
   qcd::Ctx a{};
   a.links = B->links + L.link_off;
-  a.g = {L.Ns, L.Nt, L.Vh, L.plane};
+  a.g = {L.Ns, L.Nt, L.Vh, 0, L.plane};
   cudaError_t e = B->ops->to_canonical(a, tmp, B->stream);
   if (e == cudaSuccess) e = cudaMemcpyAsync(host_out, tmp, bytes, cudaMemcpyDeviceToHost, B->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(B->stream);
@@ -715,7 +715,7 @@ int qcd_batch_set_links(qcd_batch* B, int index, const double* host_in) {
   BATCH_CUDA(cudaMalloc(reinterpret_cast<void**>(&tmp), bytes));
   qcd::Ctx a{};
   a.links = B->links + L.link_off;
-  a.g = {L.Ns, L.Nt, L.Vh, L.plane};
+  a.g = {L.Ns, L.Nt, L.Vh, 0, L.plane};
   cudaError_t e = cudaMemcpyAsync(tmp, host_in, bytes, cudaMemcpyHostToDevice, B->stream);
   if (e == cudaSuccess) e = B->ops->from_canonical(a, tmp, B->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(B->stream);

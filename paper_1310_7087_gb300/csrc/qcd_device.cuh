@@ -378,12 +378,21 @@ struct Site {
 __device__ __forceinline__ Site site_of(const Geom& g, int parity, int h) {
   int r = 2 * h;
   Site c;
-  const int x0 = r % g.Ns;
-  r /= g.Ns;
-  c.y = r % g.Ns;
-  r /= g.Ns;
-  c.z = r % g.Ns;
-  c.t = r / g.Ns;
+  int x0;
+  if (g.pow2) {  // the same decoding by shifts and masks (uniform branch)
+    const int ls = g.pow2 & 255, m = g.Ns - 1;
+    x0 = r & m;
+    c.y = (r >> ls) & m;
+    c.z = (r >> (2 * ls)) & m;
+    c.t = r >> (3 * ls);
+  } else {
+    x0 = r % g.Ns;
+    r /= g.Ns;
+    c.y = r % g.Ns;
+    r /= g.Ns;
+    c.z = r % g.Ns;
+    c.t = r / g.Ns;
+  }
   c.x = x0 + ((parity + c.y + c.z + c.t) & 1);
   return c;
 }
@@ -468,12 +477,21 @@ __device__ __forceinline__ LexSite lex_site(const Ctx& a, int parity, int h) {
 __device__ __forceinline__ LexSite lex_site_ytz(const Geom& g, int parity, int i) {
   int r = 2 * i;
   LexSite x;
-  const int x0 = r % g.Ns;
-  r /= g.Ns;
-  x.c[1] = r % g.Ns;
-  r /= g.Ns;
-  x.c[3] = r % g.Nt;
-  x.c[2] = r / g.Nt;
+  int x0;
+  if (g.pow2) {  // the same decoding by shifts and masks (uniform branch)
+    const int ls = g.pow2 & 255, lt = (g.pow2 >> 8) & 255, m = g.Ns - 1;
+    x0 = r & m;
+    x.c[1] = (r >> ls) & m;
+    x.c[3] = (r >> (2 * ls)) & (g.Nt - 1);
+    x.c[2] = r >> (2 * ls + lt);
+  } else {
+    x0 = r % g.Ns;
+    r /= g.Ns;
+    x.c[1] = r % g.Ns;
+    r /= g.Ns;
+    x.c[3] = r % g.Nt;
+    x.c[2] = r / g.Nt;
+  }
   x.c[0] = x0 + ((parity + x.c[1] + x.c[2] + x.c[3]) & 1);
   x.s = x.c[0] + g.Ns * (x.c[1] + g.Ns * (x.c[2] + g.Ns * x.c[3]));
   return x;

@@ -11,8 +11,20 @@ namespace qcd {
 struct GeomH {
   int Ns, Nt;
   int Vh;
+  int pow2;  // log2(Ns) | log2(Nt) << 8 | 1 << 16 when Ns and Nt are powers of two
+             // (site decoding by shifts and masks), else 0 (by division)
   int64_t plane;
 };
+
+inline int geom_pow2_code(int Ns, int Nt) {
+  auto lg = [](int n) {
+    int l = 0;
+    while ((1 << l) < n) ++l;
+    return (1 << l) == n ? l : -1;
+  };
+  const int ls = lg(Ns), lt = lg(Nt);
+  return ls >= 0 && lt >= 0 ? (ls | (lt << 8) | (1 << 16)) : 0;
+}
 
 // Everything a kernel launch needs for one lattice.  Device pointers only.
 struct Ctx {
