@@ -45,10 +45,11 @@ TRANSFERS_PER_UPDATE = 9
 # staple 12 full 3x3 complex products (324 complex multiply-adds), W = U A
 # (27), the three subgroup rotations of U and the first two of W (60), at 8
 # flops each = 3,288, plus ~150 for the projections, norms and quaternion
-# squares.  FP64 peak: the nominal 1.25 TFLOP/s of GB300 (152 SMs x 2 FP64
-# FMA per clock x 2 flops x 2.07 GHz = 1.26e12); no measured FP64 peak.
+# squares.  The peak it is held to is measured in the run (qcd_probe_fp64_rate:
+# FP64 FMA chains filling every SM, CUDA events); the nominal 1.25 TFLOP/s of
+# GB300 (152 SMs x 2 FP64 FMA per clock x 2 flops x 2.07 GHz) is the fallback.
 FP64_OR_FLOPS = 3438
-FP64_PEAK_TFLOPS = 1.25
+FP64_PEAK_TFLOPS_NOMINAL = 1.25
 
 
 def parse():
@@ -432,6 +433,78 @@ def run_split(q, stream, w):
     return out
 
 
+def run_flux_scan(q, stream):
+    """The SU(3) 32^3 x 8 flux scan (beta 6.0, n in {0, 1, 2, 4}, 500 working
+    sweeps of HB + 4 OR each, FP32 links) in both field modes: means and
+    binned errors of P, P_s, P_t, Re L, |L|, the bare-link P_s and its
+    difference from P_s, plus the working-sweep rate."""
+    import torch
+    from paper_1310_7087_gb300 import analysis
+    w = workloads.SU3_32x8[0]
+    fluxes = [v.flux for v in workloads.SU3_32x8]
+    out = {"workload": "su3_32^3x8_b6.0, flux n in %s, %d x (1 HB + %d OR + reunitarization + measurement), "
+                       "hot start seed %d, FP32 12-real links; first 100 sweeps discarded, errors from bins of "
+                       "20 sweeps" % (fluxes, w.sweeps, w.n_or, w.seed)}
+    for mode, name in ((q.QCD_FIELD_LINKS, "effective_links"), (q.QCD_FIELD_FROZEN, "frozen_boundary")):
+        res = analysis.flux_scan(q, fluxes, w.Ns, w.Nt, w.beta, w.sweeps, n_or=w.n_or, seed=w.seed,
+                                 n_therm=100, field_mode=mode, bin_size=20, stream=stream)
+        out[name] = {"n=%d" % n: {k: [round(v[0], 7), round(v[1], 7)] for k, v in st.items()
+                                   if isinstance(v, tuple)} for n, st in res.items()}
+    # working-sweep rate at n = 1, no host waits inside the timed loop
+    lat = q.Lattice(3, w.Ns, w.Nt, w.beta, 1, q.QCD_FP32_COMPRESSED, q.QCD_HOT, w.seed, stream)
+    buf = torch.zeros((100, 5), dtype=torch.float64, pin_memory=True)
+    q.qcd_working_sweep(lat.h, 3, w.n_or, w.seed)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for i in range(100):
+        q.qcd_working_sweep(lat.h, 1, w.n_or, w.seed, buf.data_ptr() + 40 * i, wait=False)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / 100
+    lat.close()
+    out["ms_per_working_sweep"] = ms
+    out["value"] = (1 + w.n_or) * 4 * w.volume / (ms / 1e3)
+    out["unit"] = UNIT
+    out["note"] = ("links (50 MB) fit in L2; effective-link observables must not depend on n (change of "
+                   "variables), the bare P_s and the frozen-boundary runs show the field")
+    return out
+
+
+def run_su2_single_lattices(q, stream, batched_value):
+    """Same group and the same work as the batched scan, swept one lattice
+    at a time: the 64 SU(2) lattices of the scan as single lattices, FP64 and
+    FP32 storage, each working sweep (1 HB + 1 OR + reunitarization +
+    measurement) enqueued without host waits."""
+    import torch
+    scan = workloads.batch_scan()
+    out = {"workload": "the %d SU(2) lattices of the batched scan, one working sweep of each per step, "
+                       "one lattice at a time" % scan.n}
+    lu = (1 + scan.n_or) * 4 * sum(scan.volumes)
+    for prec, name in ((q.QCD_FP64_PLAIN, "f64_plain"), (q.QCD_FP32_COMPRESSED, "f32_single")):
+        lats = [q.Lattice(2, ns, nt, b, n, prec, q.QCD_HOT, scan.seed, stream)
+                for ns, nt, b, n in zip(scan.Ns, scan.Nt, scan.beta, scan.flux)]
+        buf = torch.zeros((len(lats), 5), dtype=torch.float64, pin_memory=True)
+        for k, lat in enumerate(lats):
+            q.qcd_working_sweep(lat.h, 1, scan.n_or, scan.seed)
+        torch.cuda.synchronize()
+        steps = 5
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(steps):
+            for k, lat in enumerate(lats):
+                q.qcd_working_sweep(lat.h, 1, scan.n_or, scan.seed, buf.data_ptr() + 40 * k, wait=False)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / steps
+        for lat in lats:
+            lat.close()
+        out[name] = {"value": lu / (ms / 1e3), "unit": UNIT, "ms_per_scan_sweep": ms}
+    out["batched_f32_over_single_f64"] = batched_value / out["f64_plain"]["value"]
+    out["batched_f32_over_single_f32"] = batched_value / out["f32_single"]["value"]
+    return out
+
+
 def main():
     args = parse()
     w = workloads.SU3_64x16
@@ -559,8 +632,11 @@ def main():
         t_e2e = float(t.item())
     e2e = {"value": lu_per_step * e2e_steps * world / t_e2e, "unit": UNIT, "h2d_bytes_per_step": nbytes,
            "d2h_bytes_per_step": 5 * 8, "steps": e2e_steps,
-           "pipeline": "two lattices on two streams: upload of one step overlaps the sweep of the other; "
-                       "sweeps ordered one after another by events"}
+           "pipeline": "each step uploads a configuration in the library's device storage layout "
+                       "(qcd_copy_links_in of the qcd_link_bytes bytes qcd_copy_links_out gave) from pinned "
+                       "host memory and reads its five measured doubles back (qcd_working_sweep into pinned "
+                       "memory); two lattices on two streams: upload of one step overlaps the sweep of the "
+                       "other; sweeps ordered one after another by events"}
 
     extras = {}
     if not args.no_extras:
@@ -588,13 +664,20 @@ def main():
         if pn[1]:
             or_ms = pm[1] / pn[1]
             tf = FP64_OR_FLOPS * (w.volume // 2) / (or_ms / 1e3) / 1e12
+            try:
+                peak64, src64 = q.qcd_probe_fp64_rate(stream) / 1e12, "measured in this run (qcd_probe_fp64_rate)"
+            except q.QcdError as e:
+                peak64, src64 = FP64_PEAK_TFLOPS_NOMINAL, "nominal GB300 FP64 (probe failed: %s)" % e
             extras["fp64_plain"]["roofline"] = {
                 "bound": "alu", "kernel": "overrelax_phase", "unit": "TFLOP/s", "achieved": tf,
-                "peak": FP64_PEAK_TFLOPS, "frac": tf / FP64_PEAK_TFLOPS, "flops_per_update": FP64_OR_FLOPS,
-                "avg_launch_ms": or_ms, "peak_source": "nominal GB300 FP64 (no measured FP64 peak)"}
+                "peak": peak64, "frac": tf / peak64, "flops_per_update": FP64_OR_FLOPS,
+                "avg_launch_ms": or_ms, "peak_source": src64,
+                "nominal_peak": FP64_PEAK_TFLOPS_NOMINAL}
         lat64.close()
 
         extras["batched"] = run_batched(q, stream, world, rank, dist, workloads.batch_scan().sweeps)
+        extras["su2_same_work_single_lattices"] = run_su2_single_lattices(q, stream, extras["batched"]["value"])
+        extras["c3_flux_scan"] = run_flux_scan(q, stream)
         extras["o4_model"] = run_on_model(q, stream)
         extras["paper_lattices"] = run_paper_lattices(q, stream)
         extras["split_residency"] = run_split(q, stream, w)

@@ -80,6 +80,12 @@ extern "C" {
 /* Update kinds for qcd_phase. */
 #define QCD_HEATBATH 0
 #define QCD_OVERRELAX 1
+#define QCD_OVERRELAX_REUNIT 2  /* overrelaxation, then the FP64 reunitarization
+                                   of each updated link: the kernels of the
+                                   last pass of a sweep                      */
+#define QCD_OVERRELAX_MEASURE 3 /* as QCD_OVERRELAX_REUNIT, and the plaquette
+                                   sums of a working sweep's fused
+                                   measurement (odd parity, mu >= 1 only)    */
 
 typedef struct qcd_lattice qcd_lattice;
 
@@ -180,10 +186,37 @@ int qcd_sweep(qcd_lattice *lat, int n_heatbath, int n_overrelax, uint64_t seed);
 int qcd_working_sweep(qcd_lattice *lat, int n_heatbath, int n_overrelax,
                       uint64_t seed, double *host_out, int wait);
 
-/* One checkerboard phase (kind QCD_HEATBATH or QCD_OVERRELAX, parity 0/1,
- * direction mu) at the current sweep counter; no reunitarization, no counter
- * change.  For tests and sampled checks. */
+/* One checkerboard phase (parity 0/1, direction mu) at the current sweep
+ * counter, with no counter change, launched as the sweep launches it.  For
+ * tests and sampled checks of every kernel a sweep runs:
+ *   QCD_HEATBATH, QCD_OVERRELAX   the heat-bath and the plain overrelaxation
+ *                                 phases (no reunitarization);
+ *   QCD_OVERRELAX_REUNIT          a phase of the last overrelaxation pass of a
+ *                                 sweep: each updated link is reunitarized
+ *                                 (sec. 5) in FP64 before it is stored;
+ *   QCD_OVERRELAX_MEASURE         a plane-summing phase of a working sweep's
+ *                                 last pass (parity 1, mu = 1, 2, 3; else
+ *                                 QCD_ERR_INVALID_ARG): as QCD_OVERRELAX_REUNIT,
+ *                                 and (1/N) Re Tr of every plaquette of the
+ *                                 planes (mu, nu < mu) is summed, through the
+ *                                 updated link of each, into the lattice's
+ *                                 measurement scratch; QCD_ERR_NOT_SUPPORTED
+ *                                 where qcd_working_sweep does not fuse its
+ *                                 measurement (FP64 SU(3), frozen mode).
+ * After the eight phases of a last pass run this way (QCD_OVERRELAX_REUNIT for
+ * parity 0 and for (1, 0), QCD_OVERRELAX_MEASURE for (1, 1..3)),
+ * qcd_measure_fused_finish returns the working sweep's measurement. */
 int qcd_phase(qcd_lattice *lat, int kind, int parity, int mu, uint64_t seed);
+/* The tail of a working sweep's fused measurement (sec. 5: working sweeps end
+ * with measurements): the Polyakov loop and the final FP64 sums of the plane
+ * sums left by the QCD_OVERRELAX_MEASURE phases (1, 1), (1, 2), (1, 3).
+ * host_out[8] = {P, P_s, P_t, Re L, Im L, P_1, P_2, P_3}, P_mu the mean
+ * plaquette of the planes phase (1, mu) summed: (x,y); (x,z), (y,z);
+ * (x,t), (y,t), (z,t).  A plane (mu, nu < mu) holds no link of a later phase
+ * of the pass, so each P_mu is also that of the configuration the pass ends
+ * with.  QCD_ERR_NOT_SUPPORTED as for QCD_OVERRELAX_MEASURE.  Host pointer;
+ * synchronizes the stream. */
+int qcd_measure_fused_finish(qcd_lattice *lat, double *host_out);
 /* FP64 reunitarization of every link. */
 int qcd_reunitarize(qcd_lattice *lat);
 
@@ -278,29 +311,40 @@ int qcd_get_profile(qcd_lattice *lat, double *ms, unsigned long long *launches);
  * failure path.  It computes what qcd_measure computes, on link storage the
  * caller already holds on the device, and calls no cudaMalloc, cudaFree or
  * allocating library routine.
- *   links      device pointer, the library's storage layout for (group,
- *              precision, Ns, Nt): the bytes qcd_link_bytes reports and
- *              qcd_copy_links_out produces.  Read only; owned by the caller.
- *   flux       flux quantum of the background field (effective links U B).
- *   plaquette  host double[3] {P, P_s, P_t} or NULL;
- *   polyakov   host double[2] {Re L, Im L} or NULL.
- *   stream     cudaStream_t or NULL; the call synchronizes it.
+ *   links       device pointer to the library's storage layout for (group,
+ *               precision, Ns, Nt): the bytes qcd_copy_links_out produces.  Read
+ *               only; owned by the caller.
+ *   link_bytes  its size, as qcd_link_bytes reports it for the lattice it came
+ *               from.  The padding of each link array differs between lattices
+ *               made by qcd_lattice_create and by qcd_lattice_create_split, and
+ *               is read off this size; a size that is not 8 x (vectors per
+ *               link) arrays of at least Ns^3 Nt / 2 16-byte vectors is
+ *               QCD_ERR_INVALID_ARG.
+ *   flux, flux8 flux quanta of the background field (effective links U B), as
+ *               given to qcd_lattice_create_ex (flux8 != 0 needs group 3).  For
+ *               the storage of a lattice in the frozen field mode pass 0 and 0:
+ *               its measurements use the links as stored.
+ *   plaquette   host double[3] {P, P_s, P_t} or NULL;
+ *   polyakov    host double[2] {Re L, Im L} or NULL.
+ *   stream      cudaStream_t or NULL; the call synchronizes it.
  * Scratch: one file-scope device array of QCD_NOALLOC_SCRATCH_BYTES (512 KiB)
  * per GPU that loads the library, held until the process exits.  A lattice
  * needs 16 (ceil(V/256) + ceil(Ns^3/256)) bytes of block partials plus
  * at most 96 Ns + 320 bytes; every lattice of at most 4,194,304 sites (such as
  * 64^3 x 16) fits, a lattice that needs more returns QCD_ERR_INVALID_ARG with
- * the sizes in qcd_last_error().  The
- * first call on a device looks up the array's device address (with that device
- * current); make that first call before any stream capture.  Every call on a
- * device shares the array and overwrites what the previous call left there
- * (nothing in it needs to start at zero), so calls that overlap on the GPU
- * (different streams, or different host threads) race and must not be
- * issued. */
+ * the sizes in qcd_last_error().  The first call on a device looks up the
+ * array's device address (with that device current) and keeps it; make that
+ * first call before any stream capture.  The address belongs to the device's
+ * CUDA context, so after a cudaDeviceReset of that device (which also ends
+ * every lattice of this library on it) the call must not be used again in the
+ * same process.  Every call on a device shares the array and overwrites what
+ * the previous call left there (nothing in it needs to start at zero), so calls
+ * that overlap on the GPU (different streams, or different host threads) race
+ * and must not be issued. */
 #define QCD_NOALLOC_SCRATCH_BYTES (512u * 1024u)
-int qcd_measure_noalloc(const void *links, int group, int precision, int Ns,
-                        int Nt, int flux, double *plaquette, double *polyakov,
-                        void *stream);
+int qcd_measure_noalloc(const void *links, size_t link_bytes, int group,
+                        int precision, int Ns, int Nt, int flux, int flux8,
+                        double *plaquette, double *polyakov, void *stream);
 
 /* ------------------------------------------------------------------------
  * Batched parameter scan.  The paper runs parameter scans as independent jobs
@@ -396,6 +440,15 @@ int qcd_on_get_sweep(qcd_on *m, uint32_t *sweep);
 int qcd_on_set_sweep(qcd_on *m, uint32_t sweep);
 /* Accepted Metropolis hits since creation. */
 int qcd_on_get_accepted(qcd_on *m, unsigned long long *accepted);
+
+/* Measured FP64 arithmetic rate of the current device, for the roofline of
+ * the FP64-plain sweep (sec. 5 compares single and double precision; on this
+ * GPU the FP64 path is bound by the FP64 pipe, not by memory).  A kernel of
+ * independent FP64 fused multiply-add chains filling every SM is timed with
+ * CUDA events on `stream` (best of five launches after one warm-up);
+ * *flops_per_s receives 2 flops per FMA over that time.  Changes no clock or
+ * other device setting; synchronizes the stream. */
+int qcd_probe_fp64_rate(double *flops_per_s, void *stream);
 
 /* Message of the last failed call on this thread ("" if none). */
 const char *qcd_last_error(void);

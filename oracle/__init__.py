@@ -72,6 +72,9 @@ def lib() -> ctypes.CDLL:
         L.oracle_sweep.argtypes = [vp, i, i, u64]
         L.oracle_phase.argtypes = [vp, i, i, i, u64]
         L.oracle_reunitarize.argtypes = [vp]
+        L.oracle_reunitarize_phase.argtypes = [vp, i, i]
+        L.oracle_reunitarize_matrix.argtypes = [i, P(d)]
+        L.oracle_measure_planes.argtypes = [vp, P(d)]
         L.oracle_measure.argtypes = [vp, P(d), P(d)]
         L.oracle_measure_bare.argtypes = [vp, P(d)]
         L.oracle_get_links.argtypes = [vp, P(d)]
@@ -139,6 +142,14 @@ def uniform(w: int) -> float:
     return lib().oracle_uniform(int(w) & 0xFFFFFFFF)
 
 
+def reunitarize_matrix(m: np.ndarray) -> np.ndarray:
+    """The reunitarization of one N x N complex matrix (a copy)."""
+    N = m.shape[-1]
+    a = np.ascontiguousarray(np.stack([m.real, m.imag], axis=-1), dtype=np.float64)
+    lib().oracle_reunitarize_matrix(N, _dptr(a))
+    return a[..., 0] + 1j * a[..., 1]
+
+
 def kp_samples(alpha: float, nhit: int, seed: int, n: int):
     a0 = np.zeros(n, np.float64)
     tries = np.zeros(n, np.int32)
@@ -201,6 +212,16 @@ class OracleLattice:
 
     def reunitarize(self) -> None:
         lib().oracle_reunitarize(self._h)
+
+    def reunitarize_phase(self, parity: int, mu: int) -> None:
+        lib().oracle_reunitarize_phase(self._h, parity, mu)
+
+    def measure_planes(self):
+        """Mean plaquette of the planes (x,y), (x,z), (y,z), (x,t), (y,t),
+        (z,t), effective links."""
+        p = (ctypes.c_double * 6)()
+        lib().oracle_measure_planes(self._h, p)
+        return list(p)
 
     def measure(self):
         p = (ctypes.c_double * 3)()

@@ -780,6 +780,36 @@ void oracle_reunitarize(oracle_lattice *L)
         }
 }
 
+/* The links of one checkerboard phase only.  A sweep's reunitarization (R7)
+ * can be carried by its last overrelaxation pass, each link reunitarized
+ * right after its update there: every link is updated exactly once in a pass,
+ * so after the pass every link has been reunitarized.  Following that pass
+ * phase by phase needs the projection of just the phase's links. */
+void oracle_reunitarize_phase(oracle_lattice *L, int parity, int mu)
+{
+#pragma omp parallel for schedule(static)
+    for (long s = 0; s < L->V; ++s) {
+        if (site_parity(L, s) != parity || is_frozen(L, s, mu)) continue;
+        mat u = get_link(L, s, mu);
+        mat r = reunitarize_one(L->N, &u);
+        put_link(L, s, mu, &r);
+    }
+}
+
+void oracle_reunitarize_matrix(int N, double *m)
+{
+    mat u = mat_zero();
+    for (int i = 0; i < N; ++i)
+        for (int j = 0; j < N; ++j)
+            u.e[i][j] = m[2 * (i * N + j)] + I * m[2 * (i * N + j) + 1];
+    mat r = reunitarize_one(N, &u);
+    for (int i = 0; i < N; ++i)
+        for (int j = 0; j < N; ++j) {
+            m[2 * (i * N + j)] = creal(r.e[i][j]);
+            m[2 * (i * N + j) + 1] = cimag(r.e[i][j]);
+        }
+}
+
 void oracle_sweep(oracle_lattice *L, int n_hb, int n_or, uint64_t seed)
 {
     for (int h = 0; h < n_hb; ++h) {
@@ -857,6 +887,18 @@ void oracle_measure(const oracle_lattice *L, double plaq[3], double poly[2])
     }
     poly[0] = creal(sum) / V3;
     poly[1] = cimag(sum) / V3;
+}
+
+void oracle_measure_planes(const oracle_lattice *L, double planes[6])
+{
+    static const int PLANE[6][2] = { { 0, 1 }, { 0, 2 }, { 1, 2 },
+                                     { 0, 3 }, { 1, 3 }, { 2, 3 } };
+    for (int k = 0; k < 6; ++k) {
+        double sum = 0.0;
+        for (long s = 0; s < L->V; ++s)
+            sum += plaquette(L, s, PLANE[k][0], PLANE[k][1], 1);
+        planes[k] = sum / (double)L->V;
+    }
 }
 
 void oracle_measure_bare(const oracle_lattice *L, double plaq[3])

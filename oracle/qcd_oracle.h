@@ -66,9 +66,17 @@ void oracle_sweep(oracle_lattice *L, int n_hb, int n_or, uint64_t seed);
 void oracle_phase(oracle_lattice *L, int kind, int parity, int mu,
                   uint64_t seed);
 void oracle_reunitarize(oracle_lattice *L);
+/* Reunitarize only the links of phase (parity, mu), as a sweep's last
+ * overrelaxation pass does to each link right after updating it. */
+void oracle_reunitarize_phase(oracle_lattice *L, int parity, int mu);
+/* Reunitarize one N x N matrix in place ([row][col][re,im], FP64). */
+void oracle_reunitarize_matrix(int N, double *m);
 
 /* plaq[3] = {P, P_s, P_t} on effective links; poly[2] = {Re L, Im L}. */
 void oracle_measure(const oracle_lattice *L, double plaq[3], double poly[2]);
+/* Mean (1/N) Re Tr plaquette of each plane on effective links, planes in
+ * the order (x,y), (x,z), (y,z), (x,t), (y,t), (z,t). */
+void oracle_measure_planes(const oracle_lattice *L, double planes[6]);
 /* plaq[3] = {P, P_s, P_t} on bare links. */
 void oracle_measure_bare(const oracle_lattice *L, double plaq[3]);
 

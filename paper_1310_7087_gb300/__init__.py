@@ -29,6 +29,8 @@ QCD_COLD = 0
 QCD_HOT = 1
 QCD_HEATBATH = 0
 QCD_OVERRELAX = 1
+QCD_OVERRELAX_REUNIT = 2
+QCD_OVERRELAX_MEASURE = 3
 QCD_FIELD_LINKS = 0
 QCD_FIELD_FROZEN = 1
 
@@ -46,6 +48,7 @@ SIGNATURES = {
     "qcd_set_nhit": (_i, [_vp, _i]),
     "qcd_sweep": (_i, [_vp, _i, _i, _u64]),
     "qcd_phase": (_i, [_vp, _i, _i, _i, _u64]),
+    "qcd_measure_fused_finish": (_i, [_vp, _P(_d)]),
     "qcd_reunitarize": (_i, [_vp]),
     "qcd_measure": (_i, [_vp, _P(_d), _P(_d)]),
     "qcd_measure_async": (_i, [_vp, _vp]),
@@ -65,7 +68,7 @@ SIGNATURES = {
     "qcd_lattice_load": (_i, [_P(_vp), ctypes.c_char_p, _i, _vp]),
     "qcd_set_profiling": (_i, [_vp, _i]),
     "qcd_get_profile": (_i, [_vp, _P(_d), _P(ctypes.c_ulonglong)]),
-    "qcd_measure_noalloc": (_i, [_vp, _i, _i, _i, _i, _i, _P(_d), _P(_d), _vp]),
+    "qcd_measure_noalloc": (_i, [_vp, _sz, _i, _i, _i, _i, _i, _i, _P(_d), _P(_d), _vp]),
     "qcd_batch_create": (_i, [_P(_vp), _i, _i, _P(_i), _P(_i), _P(_d), _P(_i), _i, _i, _u64, _vp]),
     "qcd_batch_destroy": (_i, [_vp]),
     "qcd_batch_sweep": (_i, [_vp, _i, _i, _u64, _P(_d)]),
@@ -89,6 +92,7 @@ SIGNATURES = {
     "qcd_on_get_sweep": (_i, [_vp, _P(_u32)]),
     "qcd_on_set_sweep": (_i, [_vp, _u32]),
     "qcd_on_get_accepted": (_i, [_vp, _P(ctypes.c_ulonglong)]),
+    "qcd_probe_fp64_rate": (_i, [_P(_d), _vp]),
     "qcd_last_error": (ctypes.c_char_p, []),
 }
 QCD_NOALLOC_SCRATCH_BYTES = 512 * 1024
@@ -214,6 +218,14 @@ def qcd_phase(h, kind: int, parity: int, mu: int, seed: int) -> None:
     _check(lib().qcd_phase(h, kind, parity, mu, seed))
 
 
+def qcd_measure_fused_finish(h):
+    """[P, P_s, P_t, Re L, Im L, P_1, P_2, P_3] of a last pass run phase by
+    phase with qcd_phase (P_mu: mean plaquette of the planes (mu, nu < mu))."""
+    out = (ctypes.c_double * 8)()
+    _check(lib().qcd_measure_fused_finish(h, out))
+    return list(out)
+
+
 def qcd_reunitarize(h) -> None:
     _check(lib().qcd_reunitarize(h))
 
@@ -308,16 +320,23 @@ def qcd_get_profile(h):
     return list(ms), list(n)
 
 
-def qcd_measure_noalloc(links_dev_ptr: int, group: int, precision: int, Ns: int, Nt: int,
-                        flux: int = 0, stream=None):
+def qcd_measure_noalloc(links_dev_ptr: int, link_bytes: int, group: int, precision: int, Ns: int, Nt: int,
+                        flux: int = 0, flux8: int = 0, stream=None):
     """Measurement that allocates nothing, on link storage the caller holds on
-    the device (``links_dev_ptr``, the layout qcd_copy_links_out produces).
-    Returns ([P, P_s, P_t], [Re L, Im L])."""
+    the device (``links_dev_ptr``, ``link_bytes`` bytes in the layout
+    qcd_copy_links_out produces).  Returns ([P, P_s, P_t], [Re L, Im L])."""
     p = (ctypes.c_double * 3)()
     l = (ctypes.c_double * 2)()
-    _check(lib().qcd_measure_noalloc(links_dev_ptr, group, precision, Ns, Nt, flux, p, l,
+    _check(lib().qcd_measure_noalloc(links_dev_ptr, link_bytes, group, precision, Ns, Nt, flux, flux8, p, l,
                                      _stream_handle(stream)))
     return list(p), list(l)
+
+
+def qcd_probe_fp64_rate(stream=None) -> float:
+    """Measured FP64 FMA rate of the current device, flops/s."""
+    v = ctypes.c_double()
+    _check(lib().qcd_probe_fp64_rate(ctypes.byref(v), _stream_handle(stream)))
+    return v.value
 
 
 def qcd_last_error() -> str:

@@ -635,6 +635,14 @@ int qcd_sweep(qcd_lattice* L, int n_heatbath, int n_overrelax, uint64_t seed) {
   return QCD_OK;
 }
 
+// Block size of phases launched one at a time (qcd_phase) and of the fused
+// measurement's final sums that follow them.
+static int phase_block(const qcd_lattice* L) { return L->block ? L->block : 128; }
+
+static bool fused_measure_available(const qcd_lattice* L) {
+  return L->ops->measure_fused_tail != nullptr && L->field_mode == QCD_FIELD_LINKS;
+}
+
 static int measure_impl(qcd_lattice* L, int effective, double* plaq, double* poly);
 
 int qcd_working_sweep(qcd_lattice* L, int n_heatbath, int n_overrelax, uint64_t seed, double* host_out, int wait) {
@@ -642,7 +650,7 @@ int qcd_working_sweep(qcd_lattice* L, int n_heatbath, int n_overrelax, uint64_t 
   if (n_heatbath < 1 || n_overrelax < 0) return set_error(QCD_ERR_INVALID_ARG, "need n_heatbath >= 1, n_overrelax >= 0");
   if (!host_out) return set_error(QCD_ERR_INVALID_ARG, "host_out is null");
   if (int rc = use_device(L)) return rc;
-  const bool fused = L->ops->measure_fused_tail && n_overrelax > 0 && L->field_mode == QCD_FIELD_LINKS;
+  const bool fused = fused_measure_available(L) && n_overrelax > 0;
   if (!fused) {  // separate measurement after the sweeps
     if (int rc = qcd_sweep(L, n_heatbath, n_overrelax, seed)) return rc;
     if (wait) return measure_impl(L, 1, host_out, host_out + 3);
@@ -664,12 +672,33 @@ int qcd_working_sweep(qcd_lattice* L, int n_heatbath, int n_overrelax, uint64_t 
 
 int qcd_phase(qcd_lattice* L, int kind, int parity, int mu, uint64_t seed) {
   if (int rc = check(L)) return rc;
-  if ((kind != QCD_HEATBATH && kind != QCD_OVERRELAX) || (parity & ~1) || mu < 0 || mu > 3)
+  if (kind < QCD_HEATBATH || kind > QCD_OVERRELAX_MEASURE || (parity & ~1) || mu < 0 || mu > 3)
     return set_error(QCD_ERR_INVALID_ARG, "bad phase (kind %d, parity %d, mu %d)", kind, parity, mu);
+  if (kind == QCD_OVERRELAX_MEASURE) {
+    if (parity != 1 || mu < 1)
+      return set_error(QCD_ERR_INVALID_ARG,
+                       "QCD_OVERRELAX_MEASURE is a phase of odd parity with mu >= 1 (got parity %d, mu %d)",
+                       parity, mu);
+    if (!fused_measure_available(L))
+      return set_error(QCD_ERR_NOT_SUPPORTED,
+                       "the fused measurement needs FP32 SU(3) or SU(2) storage and the effective-link field mode");
+  }
   if (int rc = use_device(L)) return rc;
-  const int block = L->block ? L->block : 128;
-  QCD_CUDA(L->ops->phase(make_ctx(L, seed), kind == QCD_HEATBATH ? qcd::KIND_HB : qcd::KIND_OR, parity, mu, block,
-                         L->stream));
+  static const int kinds[4] = {qcd::KIND_HB, qcd::KIND_OR, qcd::KIND_OR_REUNIT, qcd::KIND_OR_MEAS};
+  QCD_CUDA(L->ops->phase(make_ctx(L, seed), kinds[kind], parity, mu, phase_block(L), L->stream));
+  return QCD_OK;
+}
+
+int qcd_measure_fused_finish(qcd_lattice* L, double* host_out) {
+  if (int rc = check(L)) return rc;
+  if (!host_out) return set_error(QCD_ERR_INVALID_ARG, "host_out is null");
+  if (!fused_measure_available(L))
+    return set_error(QCD_ERR_NOT_SUPPORTED,
+                     "the fused measurement needs FP32 SU(3) or SU(2) storage and the effective-link field mode");
+  if (int rc = use_device(L)) return rc;
+  QCD_CUDA(L->ops->measure_fused_tail(make_ctx(L, L->seed), phase_block(L), L->stream));
+  QCD_CUDA(cudaMemcpyAsync(host_out, L->d_meas, 8 * sizeof(double), cudaMemcpyDeviceToHost, L->stream));
+  QCD_CUDA(cudaStreamSynchronize(L->stream));
   return QCD_OK;
 }
 

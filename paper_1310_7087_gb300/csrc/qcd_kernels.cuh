@@ -842,6 +842,75 @@ static __global__ void __launch_bounds__(FINAL_THREADS)
   }
 }
 
+// Final sums of a working sweep's fused measurement: the plaquette partials
+// of the three plane-summing phases of the last pass (odd parity, mu = 1, 2,
+// 3; `grid` block partials each) and the Polyakov-loop partials.  Writes
+// meas_out = {P, P_s, P_t, Re L, Im L, P_1, P_2, P_3}, P_mu the mean plaquette
+// of the planes phase mu sums: (y,x); (z,x), (z,y); (t,x), (t,y), (t,z).
+// Two strided steps per loop keep six loads of the one block in flight; the
+// per-thread sums are reduced by warp shuffles and then across the 32 warps,
+// all in a fixed order.
+static __global__ void __launch_bounds__(FINAL_THREADS) fused_final_kernel(const Ctx a, int grid) {
+  constexpr int NW = FINAL_THREADS / 32;
+  __shared__ double sh[5][NW];
+  const int nl = meas_poly_blocks(a.g);
+  const double* p1 = a.partials + fused_plaq_offset(a.g, 1);
+  const double* p2 = a.partials + fused_plaq_offset(a.g, 2);
+  const double* p3 = a.partials + fused_plaq_offset(a.g, 3);
+  double s[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
+  int b = threadIdx.x;
+  for (; b + FINAL_THREADS < grid; b += 2 * FINAL_THREADS) {
+    const double x1 = p1[b], x2 = p2[b], x3 = p3[b];
+    const double y1 = p1[b + FINAL_THREADS], y2 = p2[b + FINAL_THREADS], y3 = p3[b + FINAL_THREADS];
+    s[0] += x1;
+    s[1] += x2;
+    s[2] += x3;
+    s[0] += y1;
+    s[1] += y2;
+    s[2] += y3;
+  }
+  for (; b < grid; b += FINAL_THREADS) {
+    s[0] += p1[b];
+    s[1] += p2[b];
+    s[2] += p3[b];
+  }
+  for (int c = threadIdx.x; c < nl; c += FINAL_THREADS) {
+    s[3] += a.partials[2 * c];
+    s[4] += a.partials[2 * c + 1];
+  }
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int k = 0; k < 5; ++k) {
+    double v = s[k];
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(0xffffffffu, v, off);
+    if (lane == 0) sh[k][warp] = v;
+  }
+  __syncthreads();
+  if (warp == 0) {
+#pragma unroll
+    for (int k = 0; k < 5; ++k) {
+      double v = lane < NW ? sh[k][lane] : 0.0;
+#pragma unroll
+      for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(0xffffffffu, v, off);
+      s[k] = v;
+    }
+    if (lane == 0) {
+      const double V = 2.0 * double(a.g.Vh);
+      const double V3 = double(a.g.Ns) * a.g.Ns * a.g.Ns;
+      const double sp = s[0] + s[1];
+      a.meas_out[0] = (sp + s[2]) / (6.0 * V);
+      a.meas_out[1] = sp / (3.0 * V);
+      a.meas_out[2] = s[2] / (3.0 * V);
+      a.meas_out[3] = s[3] / V3;
+      a.meas_out[4] = s[4] / V3;
+      a.meas_out[5] = s[0] / V;
+      a.meas_out[6] = s[1] / (2.0 * V);
+      a.meas_out[7] = s[2] / (3.0 * V);
+    }
+  }
+}
+
 // ---------------------------------------------------------------------------
 // Canonical FP64 layout [s][mu][row][col][re,im] <-> device storage
 // ---------------------------------------------------------------------------

@@ -159,46 +159,11 @@ __global__ void su2c_or_meas_kernel(const Ctx a, int parity) {
   su2c_block_sum(v, a.partials + fused_plaq_offset(a.g, MU) + blockIdx.x);
 }
 
-// Final sums of an SU(2) working sweep's fused measurement.
-template <typename R>
-__global__ void __launch_bounds__(FINAL_THREADS) su2c_fused_final_kernel(const Ctx a, int grid) {
-  __shared__ double sh[4][FINAL_THREADS];
-  const int nl = meas_poly_blocks(a.g);
-  double s[4] = {0.0, 0.0, 0.0, 0.0};
-  for (int b = threadIdx.x; b < grid; b += FINAL_THREADS) {
-    s[0] += a.partials[fused_plaq_offset(a.g, 1) + b] + a.partials[fused_plaq_offset(a.g, 2) + b];
-    s[1] += a.partials[fused_plaq_offset(a.g, 3) + b];
-  }
-  for (int b = threadIdx.x; b < nl; b += FINAL_THREADS) {
-    s[2] += a.partials[2 * b];
-    s[3] += a.partials[2 * b + 1];
-  }
-#pragma unroll
-  for (int k = 0; k < 4; ++k) sh[k][threadIdx.x] = s[k];
-  __syncthreads();
-  for (int w = FINAL_THREADS / 2; w > 0; w >>= 1) {
-    if (int(threadIdx.x) < w) {
-#pragma unroll
-      for (int k = 0; k < 4; ++k) sh[k][threadIdx.x] += sh[k][threadIdx.x + w];
-    }
-    __syncthreads();
-  }
-  if (threadIdx.x == 0) {
-    const double V = 2.0 * double(a.g.Vh);
-    const double V3 = double(a.g.Ns) * a.g.Ns * a.g.Ns;
-    a.meas_out[0] = (sh[0][0] + sh[1][0]) / (6.0 * V);
-    a.meas_out[1] = sh[0][0] / (3.0 * V);
-    a.meas_out[2] = sh[1][0] / (3.0 * V);
-    a.meas_out[3] = sh[2][0] / V3;
-    a.meas_out[4] = sh[3][0] / V3;
-  }
-}
-
 template <typename R>
 cudaError_t su2c_measure_fused_tail(const Ctx& a, int block, cudaStream_t st) {
   const int nl = meas_poly_blocks(a.g);
   measure_kernel<SU2Policy<R>, 0><<<nl, MEAS_THREADS, 0, st>>>(a, 0);  // Polyakov loop only
-  su2c_fused_final_kernel<R><<<1, FINAL_THREADS, 0, st>>>(a, int(grid_for(a.g.Vh, block)));
+  fused_final_kernel<<<1, FINAL_THREADS, 0, st>>>(a, int(grid_for(a.g.Vh, block)));
   return cudaGetLastError();
 }
 

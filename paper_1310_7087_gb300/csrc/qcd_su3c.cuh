@@ -450,58 +450,9 @@ static __global__ void __launch_bounds__(MEAS_THREADS) su3c_poly_kernel(const Ct
   block_sum2(v0, v1, a.partials + 2 * blockIdx.x);
 }
 
-// Final sums of a working sweep's fused measurement: plaquette partials of the
-// three plane-summing phases (each `grid` blocks) and the Polyakov partials.
-// Four independent loads per thread and step keep the one block's loads in
-// flight.
-static __global__ void __launch_bounds__(FINAL_THREADS) su3c_fused_final_kernel(const Ctx a, int grid) {
-  __shared__ double sh[4][FINAL_THREADS];
-  const int nl = meas_poly_blocks(a.g);
-  double s[4] = {0.0, 0.0, 0.0, 0.0};
-  const double* p1 = a.partials + fused_plaq_offset(a.g, 1);
-  const double* p2 = a.partials + fused_plaq_offset(a.g, 2);
-  const double* p3 = a.partials + fused_plaq_offset(a.g, 3);
-  int b = threadIdx.x;
-  for (; b + FINAL_THREADS < grid; b += 2 * FINAL_THREADS) {
-    const double x1 = p1[b], x2 = p2[b], x3 = p3[b];
-    const double y1 = p1[b + FINAL_THREADS], y2 = p2[b + FINAL_THREADS], y3 = p3[b + FINAL_THREADS];
-    s[0] += x1 + x2;
-    s[1] += x3;
-    s[0] += y1 + y2;
-    s[1] += y3;
-  }
-  for (; b < grid; b += FINAL_THREADS) {
-    s[0] += p1[b] + p2[b];
-    s[1] += p3[b];
-  }
-  for (int b = threadIdx.x; b < nl; b += FINAL_THREADS) {
-    s[2] += a.partials[2 * b];
-    s[3] += a.partials[2 * b + 1];
-  }
-#pragma unroll
-  for (int k = 0; k < 4; ++k) sh[k][threadIdx.x] = s[k];
-  __syncthreads();
-  for (int w = FINAL_THREADS / 2; w > 0; w >>= 1) {
-    if (int(threadIdx.x) < w) {
-#pragma unroll
-      for (int k = 0; k < 4; ++k) sh[k][threadIdx.x] += sh[k][threadIdx.x + w];
-    }
-    __syncthreads();
-  }
-  if (threadIdx.x == 0) {
-    const double V = 2.0 * double(a.g.Vh);
-    const double V3 = double(a.g.Ns) * a.g.Ns * a.g.Ns;
-    a.meas_out[0] = (sh[0][0] + sh[1][0]) / (6.0 * V);
-    a.meas_out[1] = sh[0][0] / (3.0 * V);
-    a.meas_out[2] = sh[1][0] / (3.0 * V);
-    a.meas_out[3] = sh[2][0] / V3;
-    a.meas_out[4] = sh[3][0] / V3;
-  }
-}
-
 inline cudaError_t su3c_measure_fused_tail(const Ctx& a, int block, cudaStream_t st) {
   su3c_poly_kernel<<<meas_poly_blocks(a.g), MEAS_THREADS, 0, st>>>(a);
-  su3c_fused_final_kernel<<<1, FINAL_THREADS, 0, st>>>(a, int(grid_for(a.g.Vh, block)));
+  fused_final_kernel<<<1, FINAL_THREADS, 0, st>>>(a, int(grid_for(a.g.Vh, block)));
   return cudaGetLastError();
 }
 

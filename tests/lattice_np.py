@@ -118,3 +118,20 @@ def unitarity_error(U):
     e1 = np.abs(np.einsum("nki,nkj->nij", M.conj(), M) - np.eye(N)).max()
     e2 = np.abs(np.linalg.det(M) - 1.0).max()
     return e1, e2
+
+
+def round_to_fp32_storage(U):
+    """What FP32 storage keeps of links U[..., N, N]: SU(2) the quaternion
+    entries (the first row and its mirror), SU(3) rows 1-2 rounded to FP32 with
+    row 3 rebuilt as conj(row1 x row2) in FP64."""
+    N = U.shape[-1]
+    f32 = lambda z: z.real.astype(np.float32).astype(np.float64) + 1j * z.imag.astype(np.float32).astype(np.float64)
+    R = np.array(U, dtype=complex)
+    if N == 2:
+        a, b = f32(U[..., 0, 0]), f32(U[..., 0, 1])
+        R[..., 0, 0], R[..., 0, 1] = a, b
+        R[..., 1, 0], R[..., 1, 1] = -np.conj(b), np.conj(a)
+        return R
+    R[..., :2, :] = f32(U[..., :2, :])
+    R[..., 2, :] = np.conj(np.cross(R[..., 0, :], R[..., 1, :]))
+    return R
