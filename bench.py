@@ -63,8 +63,12 @@ def parse():
                     help="skip the FP64-plain and batched-scan side measurements")
     ap.add_argument("--batch-only", action="store_true",
                     help="time only the batched 64-lattice scan (--steps sweeps in one launch)")
+    ap.add_argument("--batch-copies", type=int, default=1,
+                    help="with --batch-only: repeat the scan's lattice list (8 copies outgrow L2)")
     ap.add_argument("--Ns", type=int, default=None, help="override the spatial extent (small profiling cases)")
     ap.add_argument("--Nt", type=int, default=None, help="override the time extent (small profiling cases)")
+    ap.add_argument("--storage", choices=["fp32", "fp64"], default="fp32",
+                    help="link storage of the timed lattice (fp64: FP64 18-real, for profiling the FP64 kernels)")
     return ap.parse_args()
 
 
@@ -304,12 +308,20 @@ def config_of(w, storage):
             "l2": "links larger than L2 (no flush between steps)"}
 
 
-def run_batched(q, stream, world, rank, dist, sweeps):
+def run_batched(q, stream, world, rank, dist, sweeps, copies=1):
     """Batched scan: 64 uneven SU(2) lattices, `sweeps` sweeps in one
-    persistent launch (each rank sweeps its share of the lattices)."""
+    persistent launch (each rank sweeps its share of the lattices).  With
+    copies > 1 the list of lattices is repeated (copy i drawn with seed
+    11 + i), so the links outgrow L2 and the sweep streams from HBM."""
     import torch
     from paper_1310_7087_gb300 import dist as qd
     scan = workloads.batch_scan()
+    for i in range(1, copies):
+        more = workloads.batch_scan(seed=scan.seed + i)
+        scan.Ns += more.Ns
+        scan.Nt += more.Nt
+        scan.beta += more.beta
+        scan.flux += more.flux
     mine = qd.shard(scan.volumes, world, rank)
     pick = lambda v: [v[i] for i in mine]
     bt = q.Batch(pick(scan.Ns), pick(scan.Nt), pick(scan.beta), pick(scan.flux),
@@ -326,16 +338,23 @@ def run_batched(q, stream, world, rank, dist, sweeps):
     bt_ms = qd.max_over_ranks(g0.elapsed_time(g1), "cuda")
     lu_b = qd.sum_over_ranks(float((1 + scan.n_or) * 4 * sum(pick(scan.volumes)) * sweeps), "cuda")
     threads, ctas = q.qcd_batch_get_shape(bt.h)
+    link_bytes = q.qcd_batch_link_bytes(bt.h)
+    gbs = lu_b * TRANSFERS_PER_UPDATE * LINK_BYTES[(2, 1)] / (bt_ms / 1e3) / 1e9
     out = {"workload": "batch of %d SU(2) lattices, Ns in {8,12,16,24}, Nt in {4,6,8}, beta in [2.2,2.5], "
-                       "flux 0..3 (seed %d); %d sweeps of 1 HB + %d OR + reunitarization + measurement "
-                       "in one launch" % (scan.n, scan.seed, sweeps, scan.n_or),
+                       "flux 0..3 (seeds %d..%d); %d sweeps of 1 HB + %d OR + reunitarization + measurement "
+                       "in one launch" % (scan.n, scan.seed, scan.seed + copies - 1, sweeps, scan.n_or),
            "value": lu_b / (bt_ms / 1e3), "unit": UNIT, "ms_total": bt_ms,
            "ms_per_sweep": bt_ms / sweeps, "storage": "FP32 4-real (quaternion)",
-           "links_bytes": q.qcd_batch_link_bytes(bt.h),
-           "effective_gbs": lu_b * TRANSFERS_PER_UPDATE * LINK_BYTES[(2, 1)] / (bt_ms / 1e3) / 1e9,
-           "note": "links fit in L2 (129 MB): effective bandwidth, not HBM",
+           "links_bytes": link_bytes, "effective_gbs": gbs,
            "launch": {"threads_per_cta": threads, "ctas": ctas}, "gpu_launches_per_call": 2,
            "mean_plaquette_last_sweep": float(bm[:, -1, 0].mean())}
+    if link_bytes < 129e6:
+        out["note"] = "links fit in L2 (129 MB): effective bandwidth, not HBM"
+    else:
+        peak, src = load_peaks()
+        out["hbm_frac"] = gbs / peak
+        out["note"] = ("links larger than L2: algorithmic bytes (144 B per link update) over the sweep time, "
+                       "against the %s HBM peak %.0f GB/s" % (src, peak))
     bt.close()
     return out
 
@@ -443,12 +462,13 @@ def run_flux_scan(q, stream):
     w = workloads.SU3_32x8[0]
     fluxes = [v.flux for v in workloads.SU3_32x8]
     out = {"workload": "su3_32^3x8_b6.0, flux n in %s, %d x (1 HB + %d OR + reunitarization + measurement), "
-                       "hot start seed %d, FP32 12-real links; first 100 sweeps discarded, errors from bins of "
-                       "20 sweeps" % (fluxes, w.sweeps, w.n_or, w.seed)}
+                       "hot start seed %d, FP32 12-real links; first 100 sweeps discarded; [mean, error, tau] "
+                       "with errors from the integrated autocorrelation time tau (automatic window)"
+                       % (fluxes, w.sweeps, w.n_or, w.seed)}
     for mode, name in ((q.QCD_FIELD_LINKS, "effective_links"), (q.QCD_FIELD_FROZEN, "frozen_boundary")):
         res = analysis.flux_scan(q, fluxes, w.Ns, w.Nt, w.beta, w.sweeps, n_or=w.n_or, seed=w.seed,
-                                 n_therm=100, field_mode=mode, bin_size=20, stream=stream)
-        out[name] = {"n=%d" % n: {k: [round(v[0], 7), round(v[1], 7)] for k, v in st.items()
+                                 n_therm=100, field_mode=mode, stream=stream)
+        out[name] = {"n=%d" % n: {k: [round(v[0], 7), round(v[1], 7), round(v[2], 1)] for k, v in st.items()
                                    if isinstance(v, tuple)} for n, st in res.items()}
     # working-sweep rate at n = 1, no host waits inside the timed loop
     lat = q.Lattice(3, w.Ns, w.Nt, w.beta, 1, q.QCD_FP32_COMPRESSED, q.QCD_HOT, w.seed, stream)
@@ -529,14 +549,15 @@ def main():
 
     stream = torch.cuda.current_stream()
     if args.batch_only:
-        out = run_batched(q, stream, world, rank, dist, args.steps)
+        out = run_batched(q, stream, world, rank, dist, args.steps, args.batch_copies)
         if rank == 0:
             print(json.dumps(dict(out, metric=METRIC, n_gpus=world, steps=args.steps, warmup=1,
                                   higher_is_better=True, scaling="weak", dtype="f32", data="synthetic")),
                   flush=True)
         return 0
     seed = w.seed + 1000 * rank
-    lat = q.Lattice(w.group, w.Ns, w.Nt, w.beta, w.flux, q.QCD_FP32_COMPRESSED, q.QCD_HOT, seed, stream)
+    prec = q.QCD_FP64_PLAIN if args.storage == "fp64" else q.QCD_FP32_COMPRESSED
+    lat = q.Lattice(w.group, w.Ns, w.Nt, w.beta, w.flux, prec, q.QCD_HOT, seed, stream)
     h = lat.h
     lu_per_step = (1 + w.n_or) * 4 * w.volume
 
@@ -576,7 +597,7 @@ def main():
     names = ["heatbath_phase", "overrelax_phase", "last_pass_with_reunit", "measure"]
     dom = max(range(2), key=lambda k: prof_ms[k])
     per_launch_ms = prof_ms[dom] / max(1, prof_n[dom])
-    link_b = LINK_BYTES[(w.group, 1)]
+    link_b = LINK_BYTES[(w.group, prec)]
     alg_bytes = TRANSFERS_PER_UPDATE * link_b * (w.volume // 2)
     peak, peak_src = load_peaks()
     achieved = alg_bytes / (per_launch_ms / 1e3) / 1e9
@@ -603,7 +624,7 @@ def main():
     q.qcd_copy_links_out(h, host.data_ptr(), nbytes)
     e2e_steps = max(4, min(args.steps, 40))
     stream2 = torch.cuda.Stream()
-    lat2 = q.Lattice(w.group, w.Ns, w.Nt, w.beta, w.flux, q.QCD_FP32_COMPRESSED, q.QCD_HOT, seed, stream2)
+    lat2 = q.Lattice(w.group, w.Ns, w.Nt, w.beta, w.flux, prec, q.QCD_HOT, seed, stream2)
     pipe = [h, lat2.h]
     results = torch.zeros((e2e_steps, 5), dtype=torch.float64, pin_memory=True)
     for hh in pipe:  # graphs and launch shape in place before timing
@@ -676,6 +697,7 @@ def main():
         lat64.close()
 
         extras["batched"] = run_batched(q, stream, world, rank, dist, workloads.batch_scan().sweeps)
+        extras["batched_beyond_l2"] = run_batched(q, stream, world, rank, dist, 20, copies=8)
         extras["su2_same_work_single_lattices"] = run_su2_single_lattices(q, stream, extras["batched"]["value"])
         extras["c3_flux_scan"] = run_flux_scan(q, stream)
         extras["o4_model"] = run_on_model(q, stream)
@@ -690,9 +712,10 @@ def main():
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": t_ms / args.steps, "higher_is_better": True,
-                "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+                "scaling": "weak", "vs_baseline": None, "dtype": "f64" if args.storage == "fp64" else "f32",
                 "data": "synthetic: hot start (Haar links from Philox seed %d), no dataset" % w.seed,
-                "config": dict(config_of(w, "FP32 12-real (rows 1-2, row 3 rebuilt)"),
+                "config": dict(config_of(w, "FP64 18-real" if args.storage == "fp64"
+                                         else "FP32 12-real (rows 1-2, row 3 rebuilt)"),
                                parallelism="replicas" if world > 1 else "single GPU",
                                block=q.qcd_get_block(h)),
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks.summary(),

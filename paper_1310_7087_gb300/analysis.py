@@ -25,14 +25,46 @@ def binned(x, bin_size: int):
     return float(m.mean()), float(m.std(ddof=1) / np.sqrt(n))
 
 
+def tau_int(x, c: float = 6.0) -> float:
+    """Integrated autocorrelation time of a Monte Carlo series, in units of
+    its spacing, with the automatic window of Madras and Sokal (J. Stat. Phys.
+    50 (1988) 109): tau(W) = 1/2 + sum_{k=1..W} rho(k), W the smallest window
+    with W >= c tau(W)."""
+    x = np.asarray(x, dtype=np.float64)
+    n = len(x)
+    d = x - x.mean()
+    var = float(d @ d) / n
+    if n < 4 or var == 0.0:
+        return 0.5
+    f = np.fft.rfft(d, 2 * n)
+    acov = np.fft.irfft(f * np.conj(f))[:n] / np.arange(n, 0, -1)
+    rho = acov / acov[0]
+    tau = 0.5
+    for w in range(1, n // 2):
+        tau += rho[w]
+        if w >= c * tau:
+            break
+    return float(max(tau, 0.5))
+
+
+def mean_error(x, c: float = 6.0):
+    """(mean, error, tau): the error of the mean of a correlated series,
+    sqrt(2 tau var / n) with tau from tau_int."""
+    x = np.asarray(x, dtype=np.float64)
+    tau = tau_int(x, c)
+    return float(x.mean()), float(np.sqrt(2.0 * tau * x.var() / len(x))), tau
+
+
 def flux_scan(q, fluxes, Ns, Nt, beta, n_sweeps, n_or=4, seed=1, n_therm=100, field_mode=0,
-              bin_size=20, bare_every=1, stream=None):
+              bare_every=1, stream=None):
     """One SU(3) FP32 chain per flux quantum n: ``n_sweeps`` working sweeps
     (1 heat-bath + n_or overrelaxation passes + reunitarization +
     measurement) from a hot start, the first ``n_therm`` discarded.
 
-    Returns {n: stats}, stats holding (mean, error) of P, P_s, P_t, Re L and
-    |L| on the links the action uses (in the effective-link mode U B, a change
+    Returns {n: stats}, stats holding (mean, error, tau) of P, P_s, P_t,
+    Re L and |L| (errors from the integrated autocorrelation time, which near
+    a deconfinement transition is long for the Polyakov loop) on the links
+    the action uses (in the effective-link mode U B, a change
     of variables of the n = 0 theory), of the bare-link P_s (U alone, measured
     every ``bare_every`` sweeps) and of its difference from P_s on the same
     configuration (the field's imprint, free of most of the configuration
@@ -54,11 +86,11 @@ def flux_scan(q, fluxes, Ns, Nt, beta, n_sweeps, n_or=4, seed=1, n_therm=100, fi
         wall = time.perf_counter() - t0
         lat.close()
         meas = series[n_therm:]
-        stats = {name: binned(col, bin_size) for name, col in
+        stats = {name: mean_error(col) for name, col in
                  (("P", meas[:, 0]), ("P_s", meas[:, 1]), ("P_t", meas[:, 2]), ("Re L", meas[:, 3]),
                   ("|L|", np.hypot(meas[:, 3], meas[:, 4])))}
-        stats["P_s bare"] = binned(bare, max(2, bin_size // bare_every))
-        stats["P_s bare - P_s"] = binned(diff, max(2, bin_size // bare_every))
+        stats["P_s bare"] = mean_error(bare)
+        stats["P_s bare - P_s"] = mean_error(diff)
         stats["series"] = series
         stats["lu_per_s_wall"] = lu * n_sweeps / wall
         out[n] = stats
