@@ -366,14 +366,24 @@ __device__ __forceinline__ void block_sum_any(double v, double* out) {
 #define QCD_SU3_REUNIT_MAXNREG 128
 #endif
 
+// Programmatic dependent launch between consecutive phases of a sweep: each
+// CTA lets the next phase's grid be scheduled as soon as it starts (so the
+// next grid is resident while this one's last wave finishes), and waits for
+// the previous phase's grid to complete, with its stores visible, before it
+// reads a link.  Without a programmatic predecessor the wait returns at once.
+__device__ __forceinline__ void pdl_launch_dependents() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
 template <int FIELD, int KIND, int MU>
 __global__ void __maxnreg__(KIND == KIND_HB          ? QCD_SU3_HB_MAXNREG
                             : KIND == KIND_OR_REUNIT ? QCD_SU3_REUNIT_MAXNREG
                                                      : QCD_SU3_PHASE_MAXNREG) su3c_phase_kernel(const Ctx a, int parity) {
+  pdl_launch_dependents();
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= a.g.Vh) return;
   const LexSite x = lex_site_ytz(a.g, parity, i);
   if (frozen_link(a, MU, x.c[3])) return;
+  pdl_wait();
   const int h = x.s >> 1;
   const M3<float> A = su3c_staple<FIELD, MU>(a, parity, x);
   su3c_update<FIELD, KIND, MU>(a, parity, h, x, A, su3c_full(su3c_load(a.links, a.g, MU, parity, h)));
@@ -392,10 +402,12 @@ __global__ void __maxnreg__(KIND == KIND_HB          ? QCD_SU3_HB_MAXNREG
 
 template <int FIELD, int MU>
 __global__ void __maxnreg__(QCD_SU3_MEAS_MAXNREG) su3c_or_meas_kernel(const Ctx a, int parity) {
+  pdl_launch_dependents();
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   double v = 0.0;
   if (i < a.g.Vh) {
     const LexSite x = lex_site_ytz(a.g, parity, i);
+    pdl_wait();
     const int h = x.s >> 1;
     M3<float> low;
     const M3<float> A = su3c_staple<FIELD, MU, true>(a, parity, x, &low);
@@ -456,10 +468,28 @@ inline cudaError_t su3c_measure_fused_tail(const Ctx& a, int block, cudaStream_t
   return cudaGetLastError();
 }
 
+// Launch with programmatic stream serialization: the kernel may be scheduled
+// before its predecessor in the stream (or in the captured graph) completes;
+// it waits in-kernel (pdl_wait) before touching the predecessor's results.
+template <typename... P>
+inline void launch_programmatic(void (*kernel)(P...), unsigned grid, int block, cudaStream_t st, const Ctx& a,
+                                int parity) {
+  cudaLaunchConfig_t cfg{};
+  cfg.gridDim = dim3(grid);
+  cfg.blockDim = dim3(unsigned(block));
+  cfg.dynamicSmemBytes = 0;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  cudaLaunchKernelEx(&cfg, kernel, a, parity);
+}
+
 template <int FIELD, int KIND, int MU>
 inline void su3c_launch_one(const Ctx& a, int parity, int block, cudaStream_t st) {
-  const unsigned grid = grid_for(a.g.Vh, block);
-  su3c_phase_kernel<FIELD, KIND, MU><<<grid, block, 0, st>>>(a, parity);
+  launch_programmatic(su3c_phase_kernel<FIELD, KIND, MU>, grid_for(a.g.Vh, block), block, st, a, parity);
 }
 
 template <int FIELD, int KIND>

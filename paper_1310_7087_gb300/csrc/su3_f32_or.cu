@@ -11,7 +11,7 @@ cudaError_t su3c_launch_or_reunit(const Ctx& a, int parity, int mu, int block, c
 
 template <int FIELD, int MU>
 inline void launch_or_meas_one(const Ctx& a, int parity, int block, cudaStream_t st) {
-  su3c_or_meas_kernel<FIELD, MU><<<grid_for(a.g.Vh, block), block, 0, st>>>(a, parity);
+  launch_programmatic(su3c_or_meas_kernel<FIELD, MU>, grid_for(a.g.Vh, block), block, st, a, parity);
 }
 
 template <int FIELD>
