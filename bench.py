@@ -338,6 +338,7 @@ def run_batched(q, stream, world, rank, dist, sweeps, copies=1):
     bt_ms = qd.max_over_ranks(g0.elapsed_time(g1), "cuda")
     lu_b = qd.sum_over_ranks(float((1 + scan.n_or) * 4 * sum(pick(scan.volumes)) * sweeps), "cuda")
     threads, ctas = q.qcd_batch_get_shape(bt.h)
+    waves, wave_bytes = q.qcd_batch_get_waves(bt.h)
     link_bytes = q.qcd_batch_link_bytes(bt.h)
     gbs = lu_b * TRANSFERS_PER_UPDATE * LINK_BYTES[(2, 1)] / (bt_ms / 1e3) / 1e9
     out = {"workload": "batch of %d SU(2) lattices, Ns in {8,12,16,24}, Nt in {4,6,8}, beta in [2.2,2.5], "
@@ -346,15 +347,18 @@ def run_batched(q, stream, world, rank, dist, sweeps, copies=1):
            "value": lu_b / (bt_ms / 1e3), "unit": UNIT, "ms_total": bt_ms,
            "ms_per_sweep": bt_ms / sweeps, "storage": "FP32 4-real (quaternion)",
            "links_bytes": link_bytes, "effective_gbs": gbs,
-           "launch": {"threads_per_cta": threads, "ctas": ctas}, "gpu_launches_per_call": 2,
+           "launch": {"threads_per_cta": threads, "ctas": ctas, "waves": waves, "wave_bytes": wave_bytes},
+           "gpu_launches_per_call": 2 + waves,
            "mean_plaquette_last_sweep": float(bm[:, -1, 0].mean())}
-    if link_bytes < 129e6:
+    if waves == 1 and link_bytes < 129e6:
         out["note"] = "links fit in L2 (129 MB): effective bandwidth, not HBM"
     else:
         peak, src = load_peaks()
-        out["hbm_frac"] = gbs / peak
-        out["note"] = ("links larger than L2: algorithmic bytes (144 B per link update) over the sweep time, "
-                       "against the %s HBM peak %.0f GB/s" % (src, peak))
+        out["alg_frac_of_hbm"] = gbs / peak
+        out["note"] = ("links larger than L2, swept in %d waves of at most %.0f MB (each wave's links stay in L2 "
+                       "across the sweeps of its launch): algorithmic bytes (144 B per link update) over the "
+                       "sweep time, against the %s HBM peak %.0f GB/s; DRAM carries far less"
+                       % (waves, wave_bytes / 1e6, src, peak))
     bt.close()
     return out
 

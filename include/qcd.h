@@ -367,7 +367,8 @@ int qcd_batch_create(qcd_batch **out, int n, int group, const int *Ns,
 int qcd_batch_destroy(qcd_batch *b);
 
 /* n_sweeps sweeps of every lattice (each: 1 heat-bath pass, n_overrelax
- * overrelaxation passes, FP64 reunitarization, measurement) in one launch.
+ * overrelaxation passes, FP64 reunitarization, measurement) in one launch
+ * per wave (see qcd_batch_set_wave_bytes; one launch when the links fit L2).
  * meas_out: host double[n][n_sweeps][5] = {P, P_s, P_t, Re L, Im L} after each
  * sweep, or NULL.  The first call chooses the launch shape (autotune over 128,
  * 256, 512 threads per CTA on a scratch copy).  Returns QCD_ERR_TIMEOUT if a
@@ -384,6 +385,16 @@ int qcd_batch_link_bytes(const qcd_batch *b, size_t *bytes);
  * resulting number of CTAs. */
 int qcd_batch_set_block(qcd_batch *b, int threads);
 int qcd_batch_get_shape(qcd_batch *b, int *threads, int *ctas);
+/* Waves.  A scan whose links outgrow L2 is swept in waves of consecutive
+ * lattices whose links fit `bytes` (default: the device's L2 size, 0 = one
+ * wave): each wave is one persistent launch that runs all the sweeps of the
+ * call on its lattices, so their links stay in L2 across the sweeps; the
+ * waves run one after another.  The lattices are independent, so the links
+ * are the same for any wave size; the measurement sums of a lattice follow
+ * its CTA group's size (equal to rounding).  get returns the number of waves
+ * and the budget. */
+int qcd_batch_set_wave_bytes(qcd_batch *b, size_t bytes);
+int qcd_batch_get_waves(qcd_batch *b, int *waves, size_t *bytes);
 /* Bound of every barrier wait, in seconds (default 2, at most 60). */
 int qcd_batch_set_wait(qcd_batch *b, double seconds);
 /* Test hook: lattice `lattice`'s barriers wait for one arrival that never

@@ -79,6 +79,8 @@ SIGNATURES = {
     "qcd_batch_set_block": (_i, [_vp, _i]),
     "qcd_batch_get_shape": (_i, [_vp, _P(_i), _P(_i)]),
     "qcd_batch_set_wait": (_i, [_vp, _d]),
+    "qcd_batch_set_wave_bytes": (_i, [_vp, _sz]),
+    "qcd_batch_get_waves": (_i, [_vp, _P(_i), _P(_sz)]),
     "qcd_batch_inject_stall": (_i, [_vp, _i]),
     "qcd_on_create": (_i, [_P(_vp), _i, _i, _i, _d, _d, _d, _i, _i, _u64, _vp]),
     "qcd_on_destroy": (_i, [_vp]),
@@ -398,6 +400,17 @@ def qcd_batch_get_shape(h):
     t, c = ctypes.c_int(), ctypes.c_int()
     _check(lib().qcd_batch_get_shape(h, ctypes.byref(t), ctypes.byref(c)))
     return t.value, c.value
+
+
+def qcd_batch_set_wave_bytes(h, nbytes: int) -> None:
+    _check(lib().qcd_batch_set_wave_bytes(h, nbytes))
+
+
+def qcd_batch_get_waves(h):
+    """(number of waves, wave budget in bytes)."""
+    w, b = ctypes.c_int(), ctypes.c_size_t()
+    _check(lib().qcd_batch_get_waves(h, ctypes.byref(w), ctypes.byref(b)))
+    return w.value, b.value
 
 
 def qcd_batch_set_wait(h, seconds: float) -> None:

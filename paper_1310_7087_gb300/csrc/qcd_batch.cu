@@ -4,7 +4,12 @@
 //
 // Each lattice owns a contiguous group of CTAs, sized in proportion to its
 // work, and its phases are separated by a barrier of that group only: lattices
-// never wait for one another and there is no grid-wide barrier.  A group of
+// never wait for one another and there is no grid-wide barrier.  A scan whose
+// links outgrow L2 is swept in waves: consecutive lattices whose links fit in
+// L2 (the wave budget) form one persistent launch that runs all the sweeps of
+// the call, and the waves follow one another in the captured graph.  The
+// lattices are independent, so each wave's links stay in L2 across its
+// sweeps instead of streaming from HBM in every phase.  A group of
 // one CTA synchronises with __syncthreads; larger groups use an arrival
 // counter in global memory with a bounded wait (time and iteration limits):
 // when it runs out the kernel records an error and returns, and the host
@@ -272,7 +277,11 @@ struct qcd_batch {
   int device = 0;
   int block = 0;        // threads per CTA; 0 = autotune on the next sweep
   int per_sm = 0;       // resident CTAs per SM used (0 = as many as fit)
-  int total_ctas = 0;
+  int total_ctas = 0;   // largest grid over the waves
+  size_t wave_budget = 0;            // link bytes per wave (0: one wave)
+  std::vector<int> wave_l0;          // first lattice of each wave, then n
+  std::vector<int> wave_cta0;        // first entry of each wave in the CTA map
+  std::vector<int> wave_ctas;        // CTAs of each wave's launch
   double wait_seconds = 2.0;
   int stall_lattice = -1;
   size_t link_bytes = 0;
@@ -325,21 +334,22 @@ int resident_ctas(qcd_batch* B, int block, int per_sm_cap) {
   return per_sm * sms;
 }
 
-// Split `capacity` CTAs over the lattices in proportion to their work
-// (largest remainder), at least one each and no more than the lattice's
-// per-phase work needs.  Fills g0/g and the CTA -> lattice map.
-int allocate_ctas(qcd_batch* B, int block, int capacity, std::vector<int>& cta_lattice) {
-  const int n = B->n;
+// Split `capacity` CTAs over the lattices l0 .. l1-1 (one wave) in proportion
+// to their work (largest remainder), at least one each and no more than the
+// lattice's per-phase work needs.  Fills g0 (relative to the wave's launch)
+// and g, and appends the wave's CTA -> lattice map.  Returns the wave's CTAs.
+int allocate_ctas(qcd_batch* B, int block, int capacity, int l0, int l1, std::vector<int>& cta_lattice) {
+  const int n = l1 - l0;
   if (capacity < n) return 0;
   double total = 0.0;
-  for (auto& L : B->lat) total += double(L.Vh);
+  for (int i = l0; i < l1; ++i) total += double(B->lat[i].Vh);
   std::vector<int> g(n, 1);
   std::vector<int> cap(n);
-  for (int i = 0; i < n; ++i) cap[i] = std::max(1, (B->lat[i].Vh + block - 1) / block);
+  for (int i = 0; i < n; ++i) cap[i] = std::max(1, (B->lat[l0 + i].Vh + block - 1) / block);
   int used = n;
   std::vector<std::pair<double, int>> rem;
   for (int i = 0; i < n; ++i) {
-    const double share = double(capacity) * double(B->lat[i].Vh) / total;
+    const double share = double(capacity) * double(B->lat[l0 + i].Vh) / total;
     const int want = std::min(cap[i], std::max(1, int(std::floor(share))));
     used += want - g[i];
     g[i] = want;
@@ -359,13 +369,30 @@ int allocate_ctas(qcd_batch* B, int block, int capacity, std::vector<int>& cta_l
     --g[k];
     --used;
   }
-  cta_lattice.clear();
+  int c0 = 0;
   for (int i = 0; i < n; ++i) {
-    B->lat[i].g0 = int(cta_lattice.size());
-    B->lat[i].g = g[i];
-    for (int c = 0; c < g[i]; ++c) cta_lattice.push_back(i);
+    B->lat[l0 + i].g0 = c0;
+    B->lat[l0 + i].g = g[i];
+    for (int c = 0; c < g[i]; ++c) cta_lattice.push_back(l0 + i);
+    c0 += g[i];
   }
-  return int(cta_lattice.size());
+  return c0;
+}
+
+// Consecutive lattices whose links fit the wave budget (at least one lattice
+// per wave; budget 0: everything in one wave).
+void form_waves(qcd_batch* B) {
+  B->wave_l0.assign(1, 0);
+  size_t bytes = 0;
+  for (int i = 0; i < B->n; ++i) {
+    const size_t b = size_t(B->ops->comps) * 8 * size_t(B->lat[i].plane) * 16;
+    if (B->wave_budget && bytes > 0 && bytes + b > B->wave_budget) {
+      B->wave_l0.push_back(i);
+      bytes = 0;
+    }
+    bytes += b;
+  }
+  B->wave_l0.push_back(B->n);
 }
 
 void drop_batch_graphs(qcd_batch* B) {
@@ -373,22 +400,31 @@ void drop_batch_graphs(qcd_batch* B) {
   B->graphs.clear();
 }
 
-// Lay out the CTA groups for `block` threads (at most `per_sm` CTAs per SM,
-// 0 = as many as fit) and upload descriptors.
+// Lay out the CTA groups of every wave for `block` threads (at most `per_sm`
+// CTAs per SM, 0 = as many as fit) and upload descriptors.
 int configure(qcd_batch* B, int block, int per_sm = 0) {
   const int capacity = resident_ctas(B, block, per_sm);
+  form_waves(B);
   std::vector<int> map;
-  const int total = allocate_ctas(B, block, capacity, map);
-  if (total == 0)
-    return batch_fail(QCD_ERR_NOT_SUPPORTED, "batch of " + std::to_string(B->n) + " lattices does not fit " +
-                                                 std::to_string(capacity) + " resident CTAs of " +
-                                                 std::to_string(block) + " threads");
-  if (size_t(total) > B->partial_ctas) {
+  B->wave_cta0.clear();
+  B->wave_ctas.clear();
+  int largest = 0;
+  for (size_t w = 0; w + 1 < B->wave_l0.size(); ++w) {
+    B->wave_cta0.push_back(int(map.size()));
+    const int got = allocate_ctas(B, block, capacity, B->wave_l0[w], B->wave_l0[w + 1], map);
+    if (got == 0)
+      return batch_fail(QCD_ERR_NOT_SUPPORTED, "wave of " + std::to_string(B->wave_l0[w + 1] - B->wave_l0[w]) +
+                                                   " lattices does not fit " + std::to_string(capacity) +
+                                                   " resident CTAs of " + std::to_string(block) + " threads");
+    B->wave_ctas.push_back(got);
+    largest = std::max(largest, got);
+  }
+  if (size_t(largest) > B->partial_ctas) {
     if (B->d_partials) cudaFree(B->d_partials);
     B->d_partials = nullptr;
     B->partial_ctas = 0;
-    BATCH_CUDA(cudaMalloc(reinterpret_cast<void**>(&B->d_partials), size_t(total) * 4 * sizeof(double)));
-    B->partial_ctas = size_t(total);
+    BATCH_CUDA(cudaMalloc(reinterpret_cast<void**>(&B->d_partials), size_t(largest) * 4 * sizeof(double)));
+    B->partial_ctas = size_t(largest);
   }
   if (B->d_cta) cudaFree(B->d_cta);
   B->d_cta = nullptr;
@@ -397,7 +433,7 @@ int configure(qcd_batch* B, int block, int per_sm = 0) {
   BATCH_CUDA(cudaMemcpyAsync(B->d_lat, B->lat.data(), B->lat.size() * sizeof(BatchLat), cudaMemcpyHostToDevice,
                              B->stream));
   BATCH_CUDA(cudaStreamSynchronize(B->stream));
-  B->total_ctas = total;
+  B->total_ctas = largest;
   B->block = block;
   B->per_sm = per_sm;
   drop_batch_graphs(B);
@@ -432,15 +468,19 @@ BatchArgs make_args(qcd_batch* B, unsigned char* links, uint64_t seed, int n_swe
   return a;
 }
 
-// Enqueue one launch: zero the counters, the persistent kernel, the sweep
-// counter advance.
-int enqueue(qcd_batch* B, const BatchArgs& a, cudaStream_t st, bool advance) {
+// Enqueue one call: zero the counters, one persistent launch per wave (each
+// runs all the sweeps of its lattices), the sweep counter advance.
+int enqueue(qcd_batch* B, const BatchArgs& a0, cudaStream_t st, bool advance) {
   BATCH_CUDA(cudaMemsetAsync(B->d_arrive, 0, B->n * sizeof(unsigned), st));
-  void* params[] = {const_cast<BatchArgs*>(&a)};
-  BATCH_CUDA(cudaLaunchCooperativeKernel(reinterpret_cast<void*>(batch_kernel_ptr(B->precision)),
-                                         dim3(B->total_ctas), dim3(B->block), params, 0, st));
+  for (size_t w = 0; w < B->wave_ctas.size(); ++w) {
+    BatchArgs a = a0;
+    a.cta_lattice = B->d_cta + B->wave_cta0[w];
+    void* params[] = {&a};
+    BATCH_CUDA(cudaLaunchCooperativeKernel(reinterpret_cast<void*>(batch_kernel_ptr(B->precision)),
+                                           dim3(B->wave_ctas[w]), dim3(B->block), params, 0, st));
+  }
   if (advance) {
-    qcd::batch_advance_kernel<<<1, 1, 0, st>>>(d_sweep(B), a.n_sweeps);
+    qcd::batch_advance_kernel<<<1, 1, 0, st>>>(d_sweep(B), a0.n_sweeps);
     BATCH_CUDA(cudaGetLastError());
   }
   return QCD_OK;
@@ -534,6 +574,12 @@ int qcd_batch_create(qcd_batch** out, int n, int group, const int* Ns, const int
   B->seed = seed;
   B->stream = static_cast<cudaStream_t>(stream);
   if (cudaGetDevice(&B->device) != cudaSuccess) return fail(batch_fail(QCD_ERR_CUDA, "cudaGetDevice failed"));
+  int l2 = 0;  // default wave budget: the device's L2
+  if (cudaDeviceGetAttribute(&l2, cudaDevAttrL2CacheSize, B->device) != cudaSuccess) {
+    cudaGetLastError();
+    l2 = 0;
+  }
+  B->wave_budget = size_t(std::max(l2, 0));
   int64_t off = 0;
   for (int i = 0; i < n; ++i) {
     if (Ns[i] < 2 || Nt[i] < 2 || (Ns[i] & 1) || (Nt[i] & 1))
@@ -617,6 +663,21 @@ int qcd_batch_set_block(qcd_batch* B, int threads) {
   if (threads != 128 && threads != 256 && threads != 512)
     return batch_fail(QCD_ERR_INVALID_ARG, "threads must be 0 (autotune), 128, 256 or 512");
   return configure(B, threads);
+}
+
+int qcd_batch_set_wave_bytes(qcd_batch* B, size_t bytes) {
+  if (!B) return batch_fail(QCD_ERR_INVALID_ARG, "null batch");
+  B->wave_budget = bytes;
+  if (B->block == 0) return QCD_OK;  // laid out with the launch shape on the next sweep
+  return configure(B, B->block, B->per_sm);
+}
+
+int qcd_batch_get_waves(qcd_batch* B, int* waves, size_t* bytes) {
+  if (!B || !waves || !bytes) return batch_fail(QCD_ERR_INVALID_ARG, "null argument");
+  if (B->wave_ctas.empty()) form_waves(B);
+  *waves = int(B->wave_l0.size()) - 1;
+  *bytes = B->wave_budget;
+  return QCD_OK;
 }
 
 int qcd_batch_get_shape(qcd_batch* B, int* threads, int* ctas) {

@@ -108,6 +108,44 @@ def test_batch_results_do_not_depend_on_launch_shape(q):
         assert np.array_equal(a, c)
 
 
+@pytest.mark.parametrize("precision", [FP64_PLAIN, FP32_COMPRESSED])
+def test_batch_waves_give_the_one_wave_results(q, precision):
+    """Waves of consecutive lattices (here forced small: at most one or two
+    lattices each) sweep every lattice as one launch does: links bit-identical,
+    measurements equal to rounding, and the barrier-timeout path still works."""
+    d = SMALL
+    out = []
+    for budget in (0, 1, 40000):
+        b = q.Batch(d.Ns, d.Nt, d.beta, d.flux, precision, HOT, 3)
+        q.qcd_batch_set_wave_bytes(b.h, budget)
+        m = b.sweep(3, 1, 3)
+        waves, got = q.qcd_batch_get_waves(b.h)
+        assert got == budget and (waves == 1 if budget == 0 else waves > 1), (budget, waves)
+        if budget == 1:
+            assert waves == d.n  # one lattice per wave
+        out.append((m, [b.get_links(i) for i in range(b.n)]))
+        b.close()
+    for k in (1, 2):
+        np.testing.assert_allclose(out[0][0], out[k][0], atol=1e-13 if precision == FP64_PLAIN else 1e-6)
+        for a, c in zip(out[0][1], out[k][1]):
+            assert np.array_equal(a, c)
+
+
+def test_batch_wave_timeout(q):
+    d = SMALL
+    b = q.Batch(d.Ns, d.Nt, d.beta, d.flux, FP32_COMPRESSED, HOT, 2)
+    q.qcd_batch_set_wave_bytes(b.h, 1)
+    b.sweep(1, 1, 2)
+    q.qcd_batch_set_wait(b.h, 0.2)
+    q.qcd_batch_inject_stall(b.h, d.n - 1)  # a lattice of the last wave
+    with pytest.raises(q.QcdError) as e:
+        b.sweep(1, 1, 2)
+    assert e.value.code == q.QCD_ERR_TIMEOUT
+    q.qcd_batch_inject_stall(b.h, -1)
+    assert np.isfinite(b.sweep(1, 1, 2)).all()
+    b.close()
+
+
 def test_batch_barrier_timeout_is_reported_and_recoverable(q):
     """A barrier that waits for an arrival that never comes runs out after
     the bounded wait; the call returns QCD_ERR_TIMEOUT and the next sweep on
