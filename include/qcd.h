@@ -214,8 +214,10 @@ int qcd_phase(qcd_lattice *lat, int kind, int parity, int mu, uint64_t seed);
  * plaquette of the planes phase (1, mu) summed: (x,y); (x,z), (y,z);
  * (x,t), (y,t), (z,t).  A plane (mu, nu < mu) holds no link of a later phase
  * of the pass, so each P_mu is also that of the configuration the pass ends
- * with.  QCD_ERR_NOT_SUPPORTED as for QCD_OVERRELAX_MEASURE.  Host pointer;
- * synchronizes the stream. */
+ * with.  The phases and this call must run with one launch shape (the block
+ * size of qcd_set_block, or the tuned one: the plane sums are one per block
+ * of the phase kernels).  QCD_ERR_NOT_SUPPORTED as for
+ * QCD_OVERRELAX_MEASURE.  Host pointer; synchronizes the stream. */
 int qcd_measure_fused_finish(qcd_lattice *lat, double *host_out);
 /* FP64 reunitarization of every link. */
 int qcd_reunitarize(qcd_lattice *lat);
