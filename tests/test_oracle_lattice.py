@@ -393,3 +393,48 @@ def test_measure_planes_cold_start_closed_form(oracle_mod, N):
     L = make(oracle_mod, N, Ns, 2, 6.0, flux=n)
     xy = 3 * flux_closed_form(N, Ns, n)[1] - 2.0
     np.testing.assert_allclose(L.measure_planes(), [xy, 1, 1, 1, 1, 1], rtol=0, atol=1e-14)
+
+
+def su3_class_moments(b, n=192):
+    """<t> and <t^2>, t = (1/3) Re Tr U, under exp(b Re Tr U) on SU(3), by the
+    Weyl integration formula over the eigenphases (th1, th2, -th1-th2)."""
+    th = 2 * np.pi * np.arange(n) / n
+    t1, t2 = np.meshgrid(th, th, indexing="ij")
+    t3 = -t1 - t2
+    tr = (np.exp(1j * t1) + np.exp(1j * t2) + np.exp(1j * t3)).real
+    vdm = (np.abs(np.exp(1j * t1) - np.exp(1j * t2)) ** 2
+           * np.abs(np.exp(1j * t1) - np.exp(1j * t3)) ** 2
+           * np.abs(np.exp(1j * t2) - np.exp(1j * t3)) ** 2)
+    w = vdm * np.exp(b * tr)
+    t = tr / 3
+    return float((w * t).sum() / w.sum()), float((w * t * t).sum() / w.sum())
+
+
+@pytest.mark.parametrize("beta", [0.4, 1.0])
+def test_su3_heatbath_conditional_distribution(oracle_mod, beta):
+    """Cabibbo-Marinari heat-bath of one link under a fixed staple A = 6 (all
+    other links the unit matrix): applied over and over, its link must follow
+    exp((beta/3) Re Tr(U A)) = exp(2 beta Re Tr U), a class function, so the
+    first two moments of (1/3) Re Tr U are Weyl integrals.  A wrong subgroup
+    coupling (alpha = 2 beta k / 3), embedding or rotation order moves them."""
+    Ns, Nt = 4, 2
+    L = make(oracle_mod, 3, Ns, Nt, beta, nhit=1000)
+    s, mu = ln.index(Ns, [1, 2, 3, 1]), 2
+    np.testing.assert_allclose(L.staple(s, mu), 6 * np.eye(3), atol=1e-14)
+    U = L.get_links()
+    n_therm, n = 200, 12000
+    t = np.empty(n)
+    for i in range(n_therm + n):
+        L.sweep_counter = i
+        new, ex = L.link_update(oracle_mod.HEATBATH, s, mu, 31)
+        assert ex == 0
+        U[s, mu] = new
+        L.set_links(U)
+        if i >= n_therm:
+            t[i - n_therm] = np.trace(new).real / 3
+    m1, m2 = su3_class_moments(2 * beta)
+    for x, ref in ((t, m1), (t * t, m2)):
+        nb = 60
+        b = x[: len(x) // nb * nb].reshape(nb, -1).mean(1)
+        err = b.std(ddof=1) / np.sqrt(nb)
+        assert abs(b.mean() - ref) < 4 * err, (b.mean(), ref, err)
