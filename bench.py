@@ -292,7 +292,8 @@ def run_reference(args, w):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic (hot start, Philox seed %d)" % w.seed,
-            "config": config_of(w, "FP64 18-real (oracle)"),
+            "config": config_of(w),
+            "run": {"storage": "FP64 18-real (oracle)", "cores": cores},
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
                              "sample": "one checkerboard phase (%d link updates) per step, cycling "
                                        "through the sweep's HB and OR phases" % Vh},
@@ -301,9 +302,11 @@ def run_reference(args, w):
     return 0
 
 
-def config_of(w, storage):
+def config_of(w):
+    """The workload, identical for both arms (how each arm stores and runs it
+    goes in the line's "run" entry)."""
     return {"workload": w.name, "group": "SU(%d)" % w.group, "lattice": "%d^3x%d" % (w.Ns, w.Nt),
-            "sites": w.volume, "beta": w.beta, "flux": w.flux, "storage": storage,
+            "sites": w.volume, "beta": w.beta, "flux": w.flux,
             "sweep": "1 HB + %d OR + reunitarization + measurement" % w.n_or,
             "l2": "links larger than L2 (no flush between steps)"}
 
@@ -718,10 +721,10 @@ def main():
                 "warmup": args.warmup, "ms_per_step": t_ms / args.steps, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "f64" if args.storage == "fp64" else "f32",
                 "data": "synthetic: hot start (Haar links from Philox seed %d), no dataset" % w.seed,
-                "config": dict(config_of(w, "FP64 18-real" if args.storage == "fp64"
-                                         else "FP32 12-real (rows 1-2, row 3 rebuilt)"),
-                               parallelism="replicas" if world > 1 else "single GPU",
-                               block=q.qcd_get_block(h)),
+                "config": config_of(w),
+                "run": {"storage": "FP64 18-real" if args.storage == "fp64"
+                        else "FP32 12-real (rows 1-2, row 3 rebuilt)",
+                        "parallelism": "replicas" if world > 1 else "single GPU", "block": q.qcd_get_block(h)},
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks.summary(),
                 "hb_lu_per_s": rates["hb"], "or_lu_per_s": rates["or"],
                 "sweeps_per_s": 1e3 * args.steps / t_ms * world,
