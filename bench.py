@@ -498,6 +498,45 @@ def run_flux_scan(q, stream):
     return out
 
 
+def run_su2_large(q, stream):
+    """SU(2) on the benchmark's 64^3 x 16 lattice (links 268 MB FP32, beyond
+    L2), working sweeps of 1 HB + 1 OR + reunitarization + measurement: the
+    SU(2) FP32 and FP64 phase kernels against the HBM roofline (144 / 288 B of
+    algorithmic traffic per link update)."""
+    import torch
+    Ns, Nt, beta = 64, 16, 2.4
+    V = Ns ** 3 * Nt
+    peak, src = load_peaks()
+    out = {"workload": "su2_64^3x16_b2.4_n1, working sweeps of 1 HB + 1 OR + reunitarization + measurement",
+           "unit": UNIT}
+    for prec, name in ((q.QCD_FP32_COMPRESSED, "f32"), (q.QCD_FP64_PLAIN, "f64")):
+        lat = q.Lattice(2, Ns, Nt, beta, 1, prec, q.QCD_HOT, 3, stream)
+        q.qcd_working_sweep(lat.h, 2, 1, 3)
+        q.qcd_set_profiling(lat.h, True)
+        torch.cuda.synchronize()
+        n = 20
+        buf = torch.zeros((n, 5), dtype=torch.float64, pin_memory=True)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for i in range(n):
+            q.qcd_working_sweep(lat.h, 1, 1, 3, buf.data_ptr() + 40 * i, wait=False)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / n
+        pm, pn = q.qcd_get_profile(lat.h)
+        q.qcd_set_profiling(lat.h, False)
+        lat.close()
+        hb_ms = pm[0] / max(1, pn[0])
+        alg = TRANSFERS_PER_UPDATE * LINK_BYTES[(2, prec)] * (V // 2)
+        out[name] = {"value": 2 * 4 * V / (ms / 1e3), "ms_per_working_sweep": ms,
+                     "heatbath_ms_per_launch": hb_ms,
+                     "heatbath_alg_gbs": alg / (hb_ms / 1e3) / 1e9,
+                     "heatbath_frac_of_hbm": alg / (hb_ms / 1e3) / 1e9 / peak,
+                     "kernel_ms": [round(m / n, 4) for m in pm], "kernel_launches": [int(c) for c in pn]}
+    out["peak_source"] = src
+    return out
+
+
 def run_su2_single_lattices(q, stream, batched_value):
     """Same group and the same work as the batched scan, swept one lattice
     at a time: the 64 SU(2) lattices of the scan as single lattices, FP64 and
@@ -706,6 +745,7 @@ def main():
         extras["batched"] = run_batched(q, stream, world, rank, dist, workloads.batch_scan().sweeps)
         extras["batched_beyond_l2"] = run_batched(q, stream, world, rank, dist, 20, copies=8)
         extras["su2_same_work_single_lattices"] = run_su2_single_lattices(q, stream, extras["batched"]["value"])
+        extras["su2_64x16"] = run_su2_large(q, stream)
         extras["c3_flux_scan"] = run_flux_scan(q, stream)
         extras["o4_model"] = run_on_model(q, stream)
         extras["paper_lattices"] = run_paper_lattices(q, stream)
