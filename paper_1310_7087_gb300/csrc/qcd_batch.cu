@@ -380,20 +380,23 @@ int allocate_ctas(qcd_batch* B, int block, int capacity, int l0, int l1, std::ve
 }
 
 // Consecutive lattices whose links fit the wave budget (at least one lattice
-// per wave; budget 0: everything in one wave).
-void form_waves(qcd_batch* B) {
-  B->wave_l0.assign(1, 0);
+// per wave; budget 0: everything in one wave): the first lattice of each
+// wave, then n.
+std::vector<int> wave_starts(const qcd_batch* B) {
+  std::vector<int> l0(1, 0);
   size_t bytes = 0;
   for (int i = 0; i < B->n; ++i) {
     const size_t b = size_t(B->ops->comps) * 8 * size_t(B->lat[i].plane) * 16;
     if (B->wave_budget && bytes > 0 && bytes + b > B->wave_budget) {
-      B->wave_l0.push_back(i);
+      l0.push_back(i);
       bytes = 0;
     }
     bytes += b;
   }
-  B->wave_l0.push_back(B->n);
+  l0.push_back(B->n);
+  return l0;
 }
+void form_waves(qcd_batch* B) { B->wave_l0 = wave_starts(B); }
 
 void drop_batch_graphs(qcd_batch* B) {
   for (auto& g : B->graphs) cudaGraphExecDestroy(g.exec);
@@ -674,8 +677,7 @@ int qcd_batch_set_wave_bytes(qcd_batch* B, size_t bytes) {
 
 int qcd_batch_get_waves(qcd_batch* B, int* waves, size_t* bytes) {
   if (!B || !waves || !bytes) return batch_fail(QCD_ERR_INVALID_ARG, "null argument");
-  if (B->wave_ctas.empty()) form_waves(B);
-  *waves = int(B->wave_l0.size()) - 1;
+  *waves = int(wave_starts(B).size()) - 1;
   *bytes = B->wave_budget;
   return QCD_OK;
 }
