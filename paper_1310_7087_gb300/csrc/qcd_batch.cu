@@ -123,16 +123,64 @@ __device__ __forceinline__ void block_sum4(double v[4], double* out) {
   __syncthreads();
 }
 
-// One phase of one lattice, this CTA's share of its sites.
-template <typename R, bool FIELD, int KIND>
+// A thread's sites h = first, first + stride, ... of one parity, walked by
+// their coordinates: r = 2 h = x0 + Ns (y + Ns (z + Ns t)) (x0 even) grows by
+// 2 stride per step, added digit by digit with carries, so no site costs a
+// division by Ns or Nt (two thirds of the scan's lattices are not powers of
+// two).  The digits of 2 first and 2 stride are found once per launch.
+struct SiteWalk {
+  int x0, y, z, t;  // digits of 2 h
+  __device__ __forceinline__ LexSite site(int parity, int h) const {
+    LexSite x;
+    x.c[0] = x0 + ((parity + y + z + t) & 1);
+    x.c[1] = y;
+    x.c[2] = z;
+    x.c[3] = t;
+    x.s = 2 * h + (x.c[0] - x0);
+    return x;
+  }
+  // d: the digits of 2 stride (d.w may exceed Nt)
+  __device__ __forceinline__ void step(int Ns, const int4& d) {
+    x0 += d.x;
+    int c = x0 >= Ns;
+    x0 -= c ? Ns : 0;
+    y += d.y + c;
+    c = y >= Ns;
+    y -= c ? Ns : 0;
+    z += d.z + c;
+    c = z >= Ns;
+    z -= c ? Ns : 0;
+    t += d.w + c;
+  }
+};
+
+// Digits (x0, y, z, t) of r = x0 + Ns (y + Ns (z + Ns t)).
+__device__ inline int4 site_digits(const Geom& g, int r) {
+  int4 d;
+  d.x = r % g.Ns;
+  r /= g.Ns;
+  d.y = r % g.Ns;
+  r /= g.Ns;
+  d.z = r % g.Ns;
+  d.w = r / g.Ns;
+  return d;
+}
+
 // One phase over this CTA's share of the lattice; returns the sum of the
 // updates' plaquette terms (KIND_OR_MEAS) in FP64.
-__device__ __forceinline__ double batch_phase(const Ctx& a, int p, int mu, int first, int stride, uint32_t sweep) {
+// The digits of 2 stride are the same for the whole CTA: they are read from
+// shared memory (d) instead of being held in registers.
+template <typename R, bool FIELD, int KIND>
+__device__ __forceinline__ double batch_phase(const Ctx& a, int p, int mu, int first, int stride, const int4* d,
+                                              uint32_t sweep) {
   double v = 0.0;
+  const int4 r0 = site_digits(a.g, 2 * first);  // once per phase: nothing held across phases
+  SiteWalk w{r0.x, r0.y, r0.z, r0.w};
   switch (mu) {
 #define QCD_BATCH_MU(MU)                                                                          \
   case MU:                                                                                        \
-    for (int h = first; h < a.g.Vh; h += stride) v += double(su2c_update<R, FIELD, KIND, MU, true>(a, p, h, sweep)); \
+    for (int h = first; h < a.g.Vh; h += stride, w.step(a.g.Ns, *d))                                  \
+      v += double(su2c_update_at<R, FIELD, KIND, MU, true>(a, p, w.site(p, h), sweep));            \
     break;
     QCD_BATCH_MU(0)
     QCD_BATCH_MU(1)
@@ -164,6 +212,9 @@ __device__ void batch_run(const BatchArgs& b, int li, const BatchLat& L, int j) 
   a.phase32 = b.phase32 + L.phase_off;
   a.exhausted = b.exhausted;
   const int first = j * blockDim.x + threadIdx.x, stride = L.g * blockDim.x;
+  __shared__ int4 step_digits;
+  if (threadIdx.x == 0) step_digits = site_digits(a.g, 2 * stride);
+  __syncthreads();
   const uint32_t sweep0 = *b.sweep0;
   const bool stall = li == b.stall_lattice;
   unsigned gen = 0;
@@ -180,7 +231,7 @@ __device__ void batch_run(const BatchArgs& b, int li, const BatchLat& L, int j) 
     const uint32_t sweep = sweep0 + uint32_t(s);
     for (int p = 0; p < 2; ++p)
       for (int mu = 0; mu < 4; ++mu) {
-        batch_phase<R, FIELD, KIND_HB>(a, p, mu, first, stride, sweep);
+        batch_phase<R, FIELD, KIND_HB>(a, p, mu, first, stride, &step_digits, sweep);
         if (!barrier()) return;
       }
     double v[4] = {0.0, 0.0, 0.0, 0.0};
@@ -190,11 +241,11 @@ __device__ void batch_run(const BatchArgs& b, int li, const BatchLat& L, int j) 
       for (int p = 0; p < 2; ++p)
         for (int mu = 0; mu < 4; ++mu) {
           if (o < b.n_or - 1) {
-            batch_phase<R, FIELD, KIND_OR>(a, p, mu, first, stride, sweep);
+            batch_phase<R, FIELD, KIND_OR>(a, p, mu, first, stride, &step_digits, sweep);
           } else if (p == 1 && mu >= 1) {
-            v[mu == 3 ? 1 : 0] += batch_phase<R, FIELD, KIND_OR_MEAS>(a, p, mu, first, stride, sweep);
+            v[mu == 3 ? 1 : 0] += batch_phase<R, FIELD, KIND_OR_MEAS>(a, p, mu, first, stride, &step_digits, sweep);
           } else {
-            batch_phase<R, FIELD, KIND_OR_REUNIT>(a, p, mu, first, stride, sweep);
+            batch_phase<R, FIELD, KIND_OR_REUNIT>(a, p, mu, first, stride, &step_digits, sweep);
           }
           if (!barrier()) return;
         }
@@ -334,40 +385,57 @@ int resident_ctas(qcd_batch* B, int block, int per_sm_cap) {
   return per_sm * sms;
 }
 
-// Split `capacity` CTAs over the lattices l0 .. l1-1 (one wave) in proportion
-// to their work (largest remainder), at least one each and no more than the
-// lattice's per-phase work needs.  Fills g0 (relative to the wave's launch)
-// and g, and appends the wave's CTA -> lattice map.  Returns the wave's CTAs.
+// Split `capacity` CTAs over the lattices l0 .. l1-1 (one wave).  A group's
+// phase lasts as long as its busiest thread, ceil(Vh / (g block)) sites, and
+// the wave as long as its slowest group, so the split minimises the largest
+// per-thread load: the smallest T whose groups g = ceil(Vh / (T block)) fit
+// `capacity` (at least one CTA each, never more than the lattice's sites
+// need).  The CTAs left over then go one at a time to the group with the
+// largest load Vh / (g block).  (For the 64-lattice scan at 608 CTAs of 256
+// threads a split in proportion to Vh gives 8 sites per thread at most, this
+// one 7, against a mean of 5.9; the sweep time stays within 1 %: the kernel
+// is held by latency and barriers more than by its busiest thread.)
+// Fills g0 (relative to the wave's launch) and g, and appends the wave's
+// CTA -> lattice map.  Returns the wave's CTAs.
 int allocate_ctas(qcd_batch* B, int block, int capacity, int l0, int l1, std::vector<int>& cta_lattice) {
   const int n = l1 - l0;
   if (capacity < n) return 0;
-  double total = 0.0;
-  for (int i = l0; i < l1; ++i) total += double(B->lat[i].Vh);
-  std::vector<int> g(n, 1);
-  std::vector<int> cap(n);
-  for (int i = 0; i < n; ++i) cap[i] = std::max(1, (B->lat[l0 + i].Vh + block - 1) / block);
-  int used = n;
-  std::vector<std::pair<double, int>> rem;
+  std::vector<int> cap(n), g(n);
+  int64_t T = 1;
   for (int i = 0; i < n; ++i) {
-    const double share = double(capacity) * double(B->lat[l0 + i].Vh) / total;
-    const int want = std::min(cap[i], std::max(1, int(std::floor(share))));
-    used += want - g[i];
-    g[i] = want;
-    rem.push_back({share - std::floor(share), i});
+    cap[i] = std::max(1, (B->lat[l0 + i].Vh + block - 1) / block);
+    T = std::max<int64_t>(T, cap[i]);  // one CTA per lattice: load ceil(Vh / block)
   }
-  std::sort(rem.begin(), rem.end(), [](auto& x, auto& y) { return x.first > y.first || (x.first == y.first && x.second < y.second); });
-  for (auto& r : rem) {
-    if (used >= capacity) break;
-    if (g[r.second] < cap[r.second]) {
-      ++g[r.second];
-      ++used;
+  auto groups = [&](int64_t t) {
+    int64_t sum = 0;
+    for (int i = 0; i < n; ++i) {
+      const int64_t per = t * block;
+      g[i] = int(std::min<int64_t>(cap[i], std::max<int64_t>(1, (B->lat[l0 + i].Vh + per - 1) / per)));
+      sum += g[i];
     }
+    return sum;
+  };
+  int64_t lo = 1, hi = T;  // groups(hi) = n <= capacity
+  while (lo < hi) {
+    const int64_t mid = (lo + hi) / 2;
+    if (groups(mid) <= capacity) hi = mid;
+    else lo = mid + 1;
   }
-  while (used > capacity) {  // floor(share) >= 1 rounding may overshoot: take from the largest
-    int k = int(std::max_element(g.begin(), g.end()) - g.begin());
-    if (g[k] <= 1) return 0;
-    --g[k];
-    --used;
+  int used = int(groups(hi));
+  while (used < capacity) {
+    int k = -1;
+    double worst = 0.0;
+    for (int i = 0; i < n; ++i) {
+      if (g[i] >= cap[i]) continue;
+      const double load = double(B->lat[l0 + i].Vh) / double(g[i]);
+      if (load > worst) {
+        worst = load;
+        k = i;
+      }
+    }
+    if (k < 0) break;
+    ++g[k];
+    ++used;
   }
   int c0 = 0;
   for (int i = 0; i < n; ++i) {

@@ -68,6 +68,13 @@ __device__ __forceinline__ Quat<R> qmul(const Quat<R>& a, const Quat<R>& b) {
   c.q3 = a.q0 * b.q3 + b.q0 * a.q3 - (a.q1 * b.q2 - a.q2 * b.q1);
   return c;
 }
+// a (c + s k), the product with the quaternion (c, 0, 0, s) (the SU(2)
+// background factor diag(e^{i phi}, e^{-i phi}) has c = cos phi, s = sin phi):
+// the 8 multiply-adds of qmul whose other factor is not zero.
+template <typename R>
+__device__ __forceinline__ Quat<R> qmul_k(const Quat<R>& a, R c, R s) {
+  return {a.q0 * c - a.q3 * s, a.q1 * c - a.q2 * s, a.q2 * c + a.q1 * s, a.q3 * c + a.q0 * s};
+}
 template <typename R>
 __device__ __forceinline__ Quat<R> qdag(const Quat<R>& a) { return {a.q0, -a.q1, -a.q2, -a.q3}; }
 template <typename R>

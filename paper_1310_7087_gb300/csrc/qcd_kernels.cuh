@@ -139,7 +139,7 @@ struct Alg {
   }
   // u B with B = diag(e^{i phi}, e^{-i phi}) = cos phi + i sin phi sigma3
   static __device__ __forceinline__ Quat<R> right_phase(const Quat<R>& u, R c, R s) {
-    return qmul(u, Quat<R>{c, R(0), R(0), s});
+    return qmul_k(u, c, s);
   }
   // Re Tr(a b^+) / N
   static __device__ __forceinline__ R retr_nd_over_n(const Quat<R>& a, const Quat<R>& b) {

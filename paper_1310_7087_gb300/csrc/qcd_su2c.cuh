@@ -16,7 +16,7 @@ __device__ __forceinline__ Quat<R> su2c_eff(const Ctx& a, int par, const LexSite
   if (FIELD && D == 1) {
     R c, s;
     load_phase<R>(a, x.c[0], c, s);
-    u = qmul(u, Quat<R>{c, R(0), R(0), s});
+    u = qmul_k(u, c, s);
   }
   return u;
 }
@@ -66,12 +66,13 @@ __device__ __forceinline__ Quat<R> su2c_staple(const Ctx& a, int p, const LexSit
 // of a working sweep's last pass) returns (1/2) Re Tr(Ut A_nu) summed over
 // nu < MU for the final link, i.e. the plaquettes of the planes (MU, nu < MU)
 // through it.
+// x: the site, of parity `parity`, with its lexicographic index and coordinates.
 template <typename R, bool FIELD, int KIND, int MU, bool CG>
-__device__ __forceinline__ R su2c_update(const Ctx& a, int parity, int h, uint32_t sweep) {
+__device__ __forceinline__ R su2c_update_at(const Ctx& a, int parity, const LexSite& x, uint32_t sweep) {
   using P = SU2Policy<R>;
   constexpr bool reunit = KIND == KIND_OR_REUNIT || KIND == KIND_OR_MEAS;
   constexpr bool meas = KIND == KIND_OR_MEAS;
-  const LexSite x = lex_site(a, parity, h);
+  const int h = x.s >> 1;
   if (frozen_link(a, MU, x.c[3])) return R(0);
   Quat<R> low{R(0), R(0), R(0), R(0)};
   const Quat<R> A = su2c_staple<R, FIELD, MU, CG, meas>(a, parity, x, &low);
@@ -79,7 +80,6 @@ __device__ __forceinline__ R su2c_update(const Ctx& a, int parity, int h, uint32
   constexpr bool phased = FIELD && MU == 1;
   R bc = R(1), bs = R(0);
   if (phased) load_phase<R>(a, x.c[0], bc, bs);
-  const Quat<R> Bd{bc, R(0), R(0), -bs};  // B^+
   Quat<R> u_new;
   bool keep = false;  // the link stays as it is (it still gets the reunitarization)
   if (KIND == KIND_HB) {
@@ -108,7 +108,7 @@ __device__ __forceinline__ R su2c_update(const Ctx& a, int parity, int h, uint32
       }
     }
     if (keep) return R(0);  // heat-bath passes carry no reunitarization
-    u_new = phased ? qmul(ut_new, Bd) : ut_new;
+    u_new = phased ? qmul_k(ut_new, bc, -bs) : ut_new;  // Ut_new B^+
   } else {
     const Quat<R> u = P::template load<CG>(a.links, a.g, MU, parity, h);
     if (k2 == R(0)) {
@@ -116,16 +116,21 @@ __device__ __forceinline__ R su2c_update(const Ctx& a, int parity, int h, uint32
       u_new = u;
     } else {
       const Quat<R> Vd = qdag(qscale(A, R(1) / q_sqrt(k2)));
-      const Quat<R> ut = phased ? qmul(u, qdag(Bd)) : u;
+      const Quat<R> ut = phased ? qmul_k(u, bc, bs) : u;
       const Quat<R> ut_new = qmul(qmul(Vd, qdag(ut)), Vd);
-      u_new = phased ? qmul(ut_new, Bd) : ut_new;
+      u_new = phased ? qmul_k(ut_new, bc, -bs) : ut_new;
     }
   }
   if (reunit) u_new = su2_reunit_value<R>(u_new);
   P::store(a.links, a.g, MU, parity, h, u_new);
   if (!meas) return R(0);
-  const Quat<R> ut_final = phased ? qmul(u_new, qdag(Bd)) : u_new;
+  const Quat<R> ut_final = phased ? qmul_k(u_new, bc, bs) : u_new;
   return qmul(ut_final, low).q0;  // (1/2) Re Tr(Ut low)
+}
+
+template <typename R, bool FIELD, int KIND, int MU, bool CG>
+__device__ __forceinline__ R su2c_update(const Ctx& a, int parity, int h, uint32_t sweep) {
+  return su2c_update_at<R, FIELD, KIND, MU, CG>(a, parity, lex_site(a, parity, h), sweep);
 }
 
 template <typename R, bool FIELD, int KIND, int MU>
