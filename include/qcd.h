@@ -383,7 +383,7 @@ int qcd_batch_get_links(qcd_batch *b, int index, double *host_out);
 int qcd_batch_set_links(qcd_batch *b, int index, const double *host_in);
 int qcd_batch_get_sweep(qcd_batch *b, uint32_t *sweep);
 int qcd_batch_link_bytes(const qcd_batch *b, size_t *bytes);
-/* Launch shape: threads per CTA (0 = autotune, or 128 / 256 / 512) and the
+/* Launch shape: threads per CTA (0 = autotune, or 64 / 128 / 256 / 512) and the
  * resulting number of CTAs. */
 int qcd_batch_set_block(qcd_batch *b, int threads);
 int qcd_batch_get_shape(qcd_batch *b, int *threads, int *ctas);

@@ -586,29 +586,37 @@ int batch_autotune(qcd_batch* B) {
   float best_ms = 1e30f;
   const int stall = B->stall_lattice;
   B->stall_lattice = -1;
-  const int shapes[][2] = {{128, 0}, {256, 0}, {256, 2}, {512, 0}, {512, 1}};
-  for (const auto& shape : shapes) {
-    const int block = shape[0], per_sm = shape[1];
-    if (configure(B, block, per_sm) != QCD_OK) {
+  // every shape is timed in two rounds and keeps its faster sweep, so that
+  // one slow trial (a clock step, a neighbour's burst) does not pick a shape
+  constexpr int kShapes = 6;
+  const int shapes[kShapes][2] = {{64, 0}, {128, 0}, {256, 0}, {256, 2}, {512, 0}, {512, 1}};
+  float shape_ms[kShapes];
+  for (float& m : shape_ms) m = 1e30f;
+  for (int round = 0; round < 2; ++round)
+    for (int si = 0; si < kShapes; ++si) {
+      const int block = shapes[si][0], per_sm = shapes[si][1];
+      if (configure(B, block, per_sm) != QCD_OK) {
+        cudaGetLastError();
+        continue;
+      }
+      BATCH_CUDA(cudaMemcpyAsync(scratch, B->links, B->link_bytes, cudaMemcpyDeviceToDevice, B->stream));
+      const BatchArgs a = make_args(B, scratch, B->seed, 1, 1, meas, exh);
+      float ms = 0.f;
+      bool ok = enqueue(B, a, B->stream, false) == QCD_OK;  // warm-up
+      ok = ok && cudaEventRecord(e0, B->stream) == cudaSuccess;
+      ok = ok && enqueue(B, a, B->stream, false) == QCD_OK;
+      ok = ok && cudaEventRecord(e1, B->stream) == cudaSuccess;
+      ok = ok && cudaEventSynchronize(e1) == cudaSuccess && cudaEventElapsedTime(&ms, e0, e1) == cudaSuccess;
+      if (check_error(B) != QCD_OK) ok = false;
+      if (ok) shape_ms[si] = std::min(shape_ms[si], ms);
       cudaGetLastError();
-      continue;
     }
-    BATCH_CUDA(cudaMemcpyAsync(scratch, B->links, B->link_bytes, cudaMemcpyDeviceToDevice, B->stream));
-    const BatchArgs a = make_args(B, scratch, B->seed, 1, 1, meas, exh);
-    float ms = 0.f;
-    bool ok = enqueue(B, a, B->stream, false) == QCD_OK;  // warm-up
-    ok = ok && cudaEventRecord(e0, B->stream) == cudaSuccess;
-    ok = ok && enqueue(B, a, B->stream, false) == QCD_OK;
-    ok = ok && cudaEventRecord(e1, B->stream) == cudaSuccess;
-    ok = ok && cudaEventSynchronize(e1) == cudaSuccess && cudaEventElapsedTime(&ms, e0, e1) == cudaSuccess;
-    if (check_error(B) != QCD_OK) ok = false;
-    if (ok && ms < best_ms) {
-      best_ms = ms;
-      best = block;
-      best_per_sm = per_sm;
+  for (int si = 0; si < kShapes; ++si)
+    if (shape_ms[si] < best_ms) {
+      best_ms = shape_ms[si];
+      best = shapes[si][0];
+      best_per_sm = shapes[si][1];
     }
-    cudaGetLastError();
-  }
   B->stall_lattice = stall;
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
@@ -731,8 +739,8 @@ int qcd_batch_set_block(qcd_batch* B, int threads) {
     B->block = 0;
     return QCD_OK;
   }
-  if (threads != 128 && threads != 256 && threads != 512)
-    return batch_fail(QCD_ERR_INVALID_ARG, "threads must be 0 (autotune), 128, 256 or 512");
+  if (threads != 64 && threads != 128 && threads != 256 && threads != 512)
+    return batch_fail(QCD_ERR_INVALID_ARG, "threads must be 0 (autotune), 64, 128, 256 or 512");
   return configure(B, threads);
 }
 
