@@ -180,15 +180,22 @@ def test_batch_bad_arguments(q):
 
 def test_batch_scan_64_lattices(q):
     """The 64-lattice scan (Ns in {8,12,16,24}, Nt in {4,6,8}, seed 11): a few
-    sweeps, then for three lattices one more sweep against the oracle from the
-    same state; every lattice's plaquette in a physical range."""
+    sweeps, then for five lattices one more sweep against the oracle from the
+    same state (the three smallest, the smallest whose Nt and the smallest
+    whose Ns is not a power of two: their threads walk several sites per
+    phase, with carries through every coordinate); every lattice's plaquette
+    in a physical range."""
     d = workloads.batch_scan()
     b = q.Batch(d.Ns, d.Nt, d.beta, d.flux, FP32_COMPRESSED, HOT, d.seed)
     m = b.sweep(5, 1, d.seed)
     assert m.shape == (64, 5, 5)
     assert np.isfinite(m).all()
     assert (m[:, -1, 0] > 0.45).all() and (m[:, -1, 0] < 0.75).all()
-    small = sorted(range(64), key=lambda i: d.volumes[i])[:3]
+    by_size = sorted(range(64), key=lambda i: d.volumes[i])
+    pow2 = lambda n: n & (n - 1) == 0
+    odd_t = next(i for i in by_size if not pow2(d.Nt[i]))
+    odd_s = next(i for i in by_size if not pow2(d.Ns[i]))
+    small = by_size[:3] + [odd_t, odd_s]
     orcs = {}
     for i in small:
         o = oracles_for(d, i)
