@@ -58,14 +58,31 @@ struct Quat {
   R q0, q1, q2, q3;
 };
 
-// Matrix product a b:  (a0 b0 - a.b,  a0 b + b0 a - a x b)
+__device__ __forceinline__ float qfma(float a, float b, float c) { return fmaf(a, b, c); }
+__device__ __forceinline__ double qfma(double a, double b, double c) { return fma(a, b, c); }
+
+// acc + a b, a b the matrix product (a0 b0 - a.b,  a0 b + b0 a - a x b): each
+// component one chain of four multiply-adds started from acc.  (Written as
+// sums of differences, the compiler may not reassociate them and spends a
+// multiply and an add more per component.)
+template <typename R>
+__device__ __forceinline__ Quat<R> qmul_add(const Quat<R>& acc, const Quat<R>& a, const Quat<R>& b) {
+  Quat<R> c;
+  c.q0 = qfma(a.q0, b.q0, qfma(-a.q1, b.q1, qfma(-a.q2, b.q2, qfma(-a.q3, b.q3, acc.q0))));
+  c.q1 = qfma(a.q0, b.q1, qfma(a.q1, b.q0, qfma(-a.q2, b.q3, qfma(a.q3, b.q2, acc.q1))));
+  c.q2 = qfma(a.q0, b.q2, qfma(a.q2, b.q0, qfma(-a.q3, b.q1, qfma(a.q1, b.q3, acc.q2))));
+  c.q3 = qfma(a.q0, b.q3, qfma(a.q3, b.q0, qfma(-a.q1, b.q2, qfma(a.q2, b.q1, acc.q3))));
+  return c;
+}
+
+// Matrix product a b: the chains above, each started from one product.
 template <typename R>
 __device__ __forceinline__ Quat<R> qmul(const Quat<R>& a, const Quat<R>& b) {
   Quat<R> c;
-  c.q0 = a.q0 * b.q0 - a.q1 * b.q1 - a.q2 * b.q2 - a.q3 * b.q3;
-  c.q1 = a.q0 * b.q1 + b.q0 * a.q1 - (a.q2 * b.q3 - a.q3 * b.q2);
-  c.q2 = a.q0 * b.q2 + b.q0 * a.q2 - (a.q3 * b.q1 - a.q1 * b.q3);
-  c.q3 = a.q0 * b.q3 + b.q0 * a.q3 - (a.q1 * b.q2 - a.q2 * b.q1);
+  c.q0 = qfma(a.q0, b.q0, qfma(-a.q1, b.q1, qfma(-a.q2, b.q2, -a.q3 * b.q3)));
+  c.q1 = qfma(a.q0, b.q1, qfma(a.q1, b.q0, qfma(-a.q2, b.q3, a.q3 * b.q2)));
+  c.q2 = qfma(a.q0, b.q2, qfma(a.q2, b.q0, qfma(-a.q3, b.q1, a.q1 * b.q3)));
+  c.q3 = qfma(a.q0, b.q3, qfma(a.q3, b.q0, qfma(-a.q1, b.q2, a.q2 * b.q1)));
   return c;
 }
 // a (c + s k), the product with the quaternion (c, 0, 0, s) (the SU(2)

@@ -132,10 +132,10 @@ struct Alg {
   static __device__ __forceinline__ Quat<R> mul(const Quat<R>& a, const Quat<R>& b) { return qmul(a, b); }
   static __device__ __forceinline__ Quat<R> mul_nd(const Quat<R>& a, const Quat<R>& b) { return qmul(a, qdag(b)); }
   static __device__ __forceinline__ void acc_nd(Quat<R>& acc, const Quat<R>& a, const Quat<R>& b) {
-    acc = qadd(acc, qmul(a, qdag(b)));
+    acc = qmul_add(acc, a, qdag(b));
   }
   static __device__ __forceinline__ void acc_dn(Quat<R>& acc, const Quat<R>& a, const Quat<R>& b) {
-    acc = qadd(acc, qmul(qdag(a), b));
+    acc = qmul_add(acc, qdag(a), b);
   }
   // u B with B = diag(e^{i phi}, e^{-i phi}) = cos phi + i sin phi sigma3
   static __device__ __forceinline__ Quat<R> right_phase(const Quat<R>& u, R c, R s) {

@@ -40,13 +40,13 @@ __device__ __forceinline__ Quat<R> su2c_staple(const Ctx& a, int p, const LexSit
     const LexSite xmn = lex_step<NU, -1>(a.g, x);                                               \
     const LexSite xpmn = lex_step<NU, -1>(a.g, xp);                                             \
     /* upper: Ut_nu(x+mu) Ut_mu(x+nu)^+ Ut_nu(x)^+ */                                           \
-    A = qadd(A, qmul(qmul(su2c_eff<R, FIELD, NU, CG>(a, p ^ 1, xp),                             \
-                          qdag(su2c_eff<R, FIELD, MU, CG>(a, p ^ 1, xpn))),                     \
-                     qdag(su2c_eff<R, FIELD, NU, CG>(a, p, x))));                               \
+    A = qmul_add(A, qmul(su2c_eff<R, FIELD, NU, CG>(a, p ^ 1, xp),                              \
+                         qdag(su2c_eff<R, FIELD, MU, CG>(a, p ^ 1, xpn))),                      \
+                 qdag(su2c_eff<R, FIELD, NU, CG>(a, p, x)));                                    \
     /* lower: (Ut_mu(x-nu) Ut_nu(x+mu-nu))^+ Ut_nu(x-nu) */                                    \
-    A = qadd(A, qmul(qdag(qmul(su2c_eff<R, FIELD, MU, CG>(a, p ^ 1, xmn),                       \
-                               su2c_eff<R, FIELD, NU, CG>(a, p, xpmn))),                        \
-                     su2c_eff<R, FIELD, NU, CG>(a, p ^ 1, xmn)));                               \
+    A = qmul_add(A, qdag(qmul(su2c_eff<R, FIELD, MU, CG>(a, p ^ 1, xmn),                        \
+                              su2c_eff<R, FIELD, NU, CG>(a, p, xpmn))),                         \
+                 su2c_eff<R, FIELD, NU, CG>(a, p ^ 1, xmn));                                    \
     break;                                                                                      \
   }
       QCD_SU2C_NU(0)
