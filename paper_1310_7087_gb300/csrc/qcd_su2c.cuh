@@ -59,6 +59,22 @@ __device__ __forceinline__ Quat<R> su2c_staple(const Ctx& a, int p, const LexSit
   return A;
 }
 
+// 1 / sqrt(k2) for k2 >= 0 (0 for k2 = 0).  FP32: the approximate reciprocal
+// square root (about 2 ulp), as in the SU(3) FP32 update; its error moves the
+// new link off the group by about 1e-7, which the reunitarization of the last
+// pass removes.  FP64: correctly rounded.
+__device__ __forceinline__ float su2_rnorm(float k2) { return k2 > 0.f ? rsqrtf(k2) : 0.f; }
+__device__ __forceinline__ double su2_rnorm(double k2) { return k2 > 0.0 ? 1.0 / sqrt(k2) : 0.0; }
+// k = sqrt(k2) and 1/k (0 for k2 = 0).
+__device__ __forceinline__ void su2_norms(float k2, float& k, float& rk) {
+  rk = su2_rnorm(k2);
+  k = k2 * rk;
+}
+__device__ __forceinline__ void su2_norms(double k2, double& k, double& rk) {
+  k = sqrt(k2);
+  rk = k > 0.0 ? 1.0 / k : 0.0;
+}
+
 // One link update: A = k V (k = sqrt(det A)); heat-bath Ut_new = X V^+ with X
 // drawn by Kennedy-Pendleton (Haar when alpha = beta k = 0), overrelaxation
 // Ut_new = V^+ Ut^+ V^+; stored U = Ut_new B^+.  KIND_OR_REUNIT and
@@ -83,7 +99,8 @@ __device__ __forceinline__ R su2c_update_at(const Ctx& a, int parity, const LexS
   Quat<R> u_new;
   bool keep = false;  // the link stays as it is (it still gets the reunitarization)
   if (KIND == KIND_HB) {
-    const R k = q_sqrt(k2);
+    R k, rk;  // sqrt(k2), 1/k
+    su2_norms(k2, k, rk);
     const R alpha = R(a.beta) * k;
     const Stream dir = make_stream(a.k0, a.k1, uint32_t(x.s), sweep, MU, 0, KIND_DIR);
     Quat<R> ut_new;
@@ -104,7 +121,7 @@ __device__ __forceinline__ R su2c_update_at(const Ctx& a, int parity, const LexS
         atomicAdd(a.exhausted, 1ull);
         keep = true;
       } else {
-        ut_new = qmul(X, qdag(qscale(A, R(1) / k)));
+        ut_new = qmul(X, qdag(qscale(A, rk)));
       }
     }
     if (keep) return R(0);  // heat-bath passes carry no reunitarization
@@ -115,7 +132,7 @@ __device__ __forceinline__ R su2c_update_at(const Ctx& a, int parity, const LexS
       if (!reunit) return R(0);
       u_new = u;
     } else {
-      const Quat<R> Vd = qdag(qscale(A, R(1) / q_sqrt(k2)));
+      const Quat<R> Vd = qdag(qscale(A, su2_rnorm(k2)));
       const Quat<R> ut = phased ? qmul_k(u, bc, bs) : u;
       const Quat<R> ut_new = qmul(qmul(Vd, qdag(ut)), Vd);
       u_new = phased ? qmul_k(ut_new, bc, -bs) : ut_new;
