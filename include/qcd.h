@@ -362,7 +362,9 @@ typedef struct qcd_batch qcd_batch;
 
 /* n lattices: Ns[i], Nt[i] even >= 2, beta[i] >= 0, flux[i]; group must be 2
  * (QCD_ERR_NOT_SUPPORTED otherwise); precision and start as for
- * qcd_lattice_create.  Arrays are host memory, read during the call. */
+ * qcd_lattice_create.  Each lattice has fewer than 2^29 sites (FP32) or 2^31
+ * (FP64), else QCD_ERR_INVALID_ARG.  Arrays are host memory, read during the
+ * call. */
 int qcd_batch_create(qcd_batch **out, int n, int group, const int *Ns,
                      const int *Nt, const double *beta, const int *flux,
                      int precision, int start, uint64_t seed, void *stream);

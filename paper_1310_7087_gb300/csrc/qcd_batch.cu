@@ -665,7 +665,11 @@ int qcd_batch_create(qcd_batch** out, int n, int group, const int* Ns, const int
       return fail(batch_fail(QCD_ERR_INVALID_ARG, "lattice " + std::to_string(i) + ": Ns, Nt must be even, >= 2"));
     if (!(beta[i] >= 0.0)) return fail(batch_fail(QCD_ERR_INVALID_ARG, "beta must be >= 0"));
     const long long V = (long long)Ns[i] * Ns[i] * Ns[i] * Nt[i];
-    if (V >= (1LL << 31)) return fail(batch_fail(QCD_ERR_INVALID_ARG, "lattice too large"));
+    // the batched kernel indexes a lattice's FP32 link arrays (8 arrays of
+    // V/2 + padding float4 each) in 32-bit arithmetic: fewer than 2^29 sites
+    if (V >= (precision == QCD_FP32_COMPRESSED ? (1LL << 29) : (1LL << 31)))
+      return fail(batch_fail(QCD_ERR_INVALID_ARG,
+                             "lattice " + std::to_string(i) + " too large for a batch (2^29 sites FP32, 2^31 FP64)"));
     BatchLat L{};
     L.Ns = Ns[i];
     L.Nt = Nt[i];

@@ -169,6 +169,18 @@ def test_batch_barrier_timeout_is_reported_and_recoverable(q):
     b.close()
 
 
+def test_batch_lattice_size_limit(q):
+    """FP32 batches index a lattice's links in 32-bit arithmetic: a lattice of
+    2^29 sites is refused before anything is allocated (128^3 x 256), FP64
+    keeps the 2^31 limit."""
+    with pytest.raises(q.QcdError) as e:
+        q.qcd_batch_create(2, [4, 128], [4, 256], [2.3, 2.3], [0, 0], FP32_COMPRESSED)
+    assert e.value.code == q.QCD_ERR_INVALID_ARG
+    with pytest.raises(q.QcdError) as e:
+        q.qcd_batch_create(2, [4, 256], [4, 128], [2.3, 2.3], [0, 0], FP64_PLAIN)
+    assert e.value.code == q.QCD_ERR_INVALID_ARG
+
+
 def test_batch_bad_arguments(q):
     with pytest.raises(q.QcdError) as e:
         q.qcd_batch_create(3, [4], [4], [1.0], [0])
