@@ -179,17 +179,6 @@ __device__ __forceinline__ Rows2 su3c_mul_dn(const M3<float>& a, const M3<float>
   return c;
 }
 
-// acc += the SU(3) matrix whose rows 0-1 are t
-__device__ __forceinline__ void su3c_acc(M3<float>& acc, const Rows2& t) {
-#pragma unroll
-  for (int c = 0; c < 3; ++c) {
-    const int c1 = (c + 1) % 3, c2 = (c + 2) % 3;
-    acc.e[0][c] = cx2(fadd2(v2(acc.e[0][c]), v2(t.e[0][c])));
-    acc.e[1][c] = cx2(fadd2(v2(acc.e[1][c]), v2(t.e[1][c])));
-    acc.e[2][c] = cx2(fadd2(v2(acc.e[2][c]), v2(cross2(t.e[0][c1], t.e[1][c2], t.e[0][c2], t.e[1][c1]))));
-  }
-}
-
 // m <- R_emb m for the 2x2 matrix of quaternion r on rows (i, j):
 // row i' = r00 row i + r01 row j, row j' = r10 row i + r11 row j.
 __device__ __forceinline__ void su3c_left_rotate(M3<float>& m, const Quat<float>& r, int i, int j) {
@@ -224,7 +213,28 @@ __device__ __forceinline__ Rows2 su3c_eff(const Ctx& a, int par, const LexSite& 
   return r;
 }
 
-// Staple sum of U_MU(x) (x of parity p) on effective links, full 3x3.
+// acc += the SU(3) matrix whose rows 0-1 are t, for an accumulator whose row
+// 2 is held conjugated: t's row 2 is conj(t0 x t1), so the conjugated row
+// gains t0 x t1, which starts the chain of its products (one paired add less
+// per element than su3c_acc).
+__device__ __forceinline__ void su3c_acc_c(M3<float>& acc, const Rows2& t) {
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    const int c1 = (c + 1) % 3, c2 = (c + 2) % 3;
+    acc.e[0][c] = cx2(fadd2(v2(acc.e[0][c]), v2(t.e[0][c])));
+    acc.e[1][c] = cx2(fadd2(v2(acc.e[1][c]), v2(t.e[1][c])));
+    XY s{ffma2(bc(t.e[1][c2].re), v2(t.e[0][c1]), v2(acc.e[2][c])), fmul2(bc(t.e[1][c2].im), v2(t.e[0][c1]))};
+    xy_sub(s, t.e[0][c2], t.e[1][c1]);
+    acc.e[2][c] = xy_mul(s);
+  }
+}
+__device__ __forceinline__ void su3c_conj_row2(M3<float>& m) {
+#pragma unroll
+  for (int c = 0; c < 3; ++c) m.e[2][c].im = -m.e[2][c].im;
+}
+
+// Staple sum of U_MU(x) (x of parity p) on effective links, full 3x3 (row 2
+// accumulated conjugated, see su3c_acc_c).
 // With SPLIT, *low receives the part of the sum over nu < MU.
 template <int FIELD, int MU, bool SPLIT = false>
 __device__ __forceinline__ M3<float> su3c_staple(const Ctx& a, int p, const LexSite& x, M3<float>* low = nullptr) {
@@ -234,7 +244,10 @@ __device__ __forceinline__ M3<float> su3c_staple(const Ctx& a, int p, const LexS
 #pragma unroll
   for (int nu = 0; nu < 4; ++nu) {
     if (nu == MU) {
-      if (SPLIT) *low = A;
+      if (SPLIT) {
+        *low = A;
+        su3c_conj_row2(*low);
+      }
       continue;
     }
     // Each branch of this switch is one static value of NU.
@@ -247,11 +260,11 @@ __device__ __forceinline__ M3<float> su3c_staple(const Ctx& a, int p, const LexS
     /* upper: Ut_nu(x+mu) Ut_mu(x+nu)^+ Ut_nu(x)^+ */                                             \
     const Rows2 x1 = su3c_mul_nd(su3c_eff<FIELD, NU>(a, p ^ 1, xp),                               \
                                  su3c_full(su3c_eff<FIELD, MU>(a, p ^ 1, xpn)));                  \
-    su3c_acc(A, su3c_mul_nd(x1, su3c_full(su3c_eff<FIELD, NU>(a, p, x))));                        \
+    su3c_acc_c(A, su3c_mul_nd(x1, su3c_full(su3c_eff<FIELD, NU>(a, p, x))));                      \
     /* lower: (Ut_mu(x-nu) Ut_nu(x+mu-nu))^+ Ut_nu(x-nu) */                                      \
     const M3<float> y = su3c_full(su3c_mul(su3c_eff<FIELD, MU>(a, p ^ 1, xmn),                   \
                                            su3c_full(su3c_eff<FIELD, NU>(a, p, xpmn))));          \
-    su3c_acc(A, su3c_mul_dn(y, su3c_full(su3c_eff<FIELD, NU>(a, p ^ 1, xmn))));                   \
+    su3c_acc_c(A, su3c_mul_dn(y, su3c_full(su3c_eff<FIELD, NU>(a, p ^ 1, xmn))));                 \
     break;                                                                                        \
   }
       QCD_SU3C_NU(0)
@@ -261,6 +274,7 @@ __device__ __forceinline__ M3<float> su3c_staple(const Ctx& a, int p, const LexS
 #undef QCD_SU3C_NU
     }
   }
+  su3c_conj_row2(A);
   return A;
 }
 
