@@ -90,13 +90,23 @@ __device__ __forceinline__ Rows2 su3c_load(const void* base, const Geom& g, int 
   return r;
 }
 
+// (-x, x): with the swapped pair of a, x (i a) = (-x a.im, x a.re).
+__device__ __forceinline__ float2 pm(float x) { return make_float2(-x, x); }
+// a b for a complex factor b given as b.re and pm(b.im): b.re a + b.im (i a),
+// one paired multiply of the swapped pair and one paired multiply-add (the
+// accumulator form xy_mul(xy_first(a, b)) takes three).
+__device__ __forceinline__ Cx<float> cmul_pm(Cx<float> a, float bre, float2 bim_pm) {
+  return cx2(ffma2(bc(bre), v2(a), fmul2(swp(v2(a)), bim_pm)));
+}
+__device__ __forceinline__ Cx<float> cmul_pm(Cx<float> a, Cx<float> b) { return cmul_pm(a, b.re, pm(b.im)); }
+
 // Right multiplication by B = diag(e^{i phi}, e^{-i phi}, 1).
 __device__ __forceinline__ void su3c_phase(Rows2& r, float c, float s) {
-  const Cx<float> p{c, s}, pc{c, -s};
+  const float2 sp = pm(s), sm = pm(-s);
 #pragma unroll
   for (int i = 0; i < 2; ++i) {
-    r.e[i][0] = xy_mul(xy_first(r.e[i][0], p));
-    r.e[i][1] = xy_mul(xy_first(r.e[i][1], pc));
+    r.e[i][0] = cmul_pm(r.e[i][0], c, sp);
+    r.e[i][1] = cmul_pm(r.e[i][1], c, sm);
   }
 }
 
@@ -208,7 +218,7 @@ __device__ __forceinline__ Rows2 su3c_eff(const Ctx& a, int par, const LexSite& 
 #pragma unroll
     for (int i = 0; i < 2; ++i)
 #pragma unroll
-      for (int k = 0; k < 3; ++k) r.e[i][k] = xy_mul(xy_first(r.e[i][k], b[k]));
+      for (int k = 0; k < 3; ++k) r.e[i][k] = cmul_pm(r.e[i][k], b[k]);
   }
   return r;
 }
@@ -304,14 +314,14 @@ __device__ __forceinline__ M3<float> su3c_update(const Ctx& a, int parity, int h
 #pragma unroll
     for (int r = 0; r < 3; ++r)
 #pragma unroll
-      for (int k = 0; k < 3; ++k) Ut.e[r][k] = xy_mul(xy_first(U.e[r][k], b[k]));
+      for (int k = 0; k < 3; ++k) Ut.e[r][k] = cmul_pm(U.e[r][k], b[k]);
   } else if (FIELD == 1 && MU == 1) {
     const float2 ph = __ldg(a.phase32 + x.c[0]);
     const Cx<float> p{ph.x, ph.y}, pc{ph.x, -ph.y};
 #pragma unroll
     for (int r = 0; r < 3; ++r) {
-      Ut.e[r][0] = xy_mul(xy_first(U.e[r][0], p));
-      Ut.e[r][1] = xy_mul(xy_first(U.e[r][1], pc));
+      Ut.e[r][0] = cmul_pm(U.e[r][0], p);
+      Ut.e[r][1] = cmul_pm(U.e[r][1], pc);
     }
   }
   M3<float> W = su3c_mul3(Ut, A);
@@ -433,8 +443,8 @@ __global__ void __maxnreg__(QCD_SU3_MEAS_MAXNREG) su3c_or_meas_kernel(const Ctx 
       const Cx<float> pp{ph.x, ph.y}, pc{ph.x, -ph.y};
 #pragma unroll
       for (int r = 0; r < 3; ++r) {
-        U.e[r][0] = xy_mul(xy_first(U.e[r][0], pp));
-        U.e[r][1] = xy_mul(xy_first(U.e[r][1], pc));
+        U.e[r][0] = cmul_pm(U.e[r][0], pp);
+        U.e[r][1] = cmul_pm(U.e[r][1], pc);
       }
     } else if (FIELD == 2 && MU == 1) {
       Cx<float> b[3];
@@ -442,7 +452,7 @@ __global__ void __maxnreg__(QCD_SU3_MEAS_MAXNREG) su3c_or_meas_kernel(const Ctx 
 #pragma unroll
       for (int r = 0; r < 3; ++r)
 #pragma unroll
-        for (int k = 0; k < 3; ++k) U.e[r][k] = xy_mul(xy_first(U.e[r][k], b[k]));
+        for (int k = 0; k < 3; ++k) U.e[r][k] = cmul_pm(U.e[r][k], b[k]);
     }
     v = double(m3_retrace_mul(U, low)) / 3.0;
   }
