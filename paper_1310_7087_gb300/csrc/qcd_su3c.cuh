@@ -288,14 +288,44 @@ __device__ __forceinline__ M3<float> su3c_staple(const Ctx& a, int p, const LexS
   return A;
 }
 
-// One Kennedy-Pendleton subgroup step of the FP32 heat-bath: the rotation
-// R = X V^+ for the normalized block wn = V, or q0 = 2 when every try failed.
-// Not inlined: the three subgroups share one copy of the sampling code.
-static __device__ __noinline__ Quat<float> su3c_kp_rotation(float alpha, int nhit, Stream tries, Stream dir,
-                                                            Quat<float> wn) {
-  Quat<float> X;
-  if (!kp_draw_dir_f32(alpha, nhit, tries, dir, X)) return {2.f, 0.f, 0.f, 0.f};
-  return qmul(X, qdag(wn));
+// The first Kennedy-Pendleton try and the direction of each subgroup do not
+// depend on the staple, so the heat-bath kernel draws them before it gathers
+// the links, while the gather's first loads are in flight.  Six floats per
+// subgroup stay live: alpha delta of try 0, u3^2 of its acceptance test, and
+// sin(theta), cos(theta), sin(phi), cos(phi) of the direction, combined with
+// the modulus in the order su2_with_delta_u uses, so the result is the same
+// to the bit as drawing them after the staple.
+struct KpFirst {
+  float e, a3, st, ct, sp, cp;
+};
+
+__device__ __forceinline__ KpFirst su3c_kp_first(const Stream& tries, const Stream& dir) {
+  float u[4], v[4];
+  tries.uniforms<float>(0u, u);
+  dir.uniforms<float>(0u, v);
+  KpFirst f;
+  // try 0 as kp_try_f32 forms it, before the division by alpha
+  const float c = __cosf(6.283185307179586f * (u[2] - 0.5f));
+  f.e = -__logf(u[1]) - __logf(u[0]) * c * c;
+  f.a3 = u[3] * u[3];
+  // the direction as su2_with_delta_u forms it
+  f.ct = 2.f * v[0] - 1.f;
+  const float q = v[0] * (1.f - v[0]);
+  f.st = 2.f * q * rsqrtf(q);
+  __sincosf(6.283185307179586f * (v[1] - 0.5f), &f.sp, &f.cp);
+  return f;
+}
+
+// Tries 1 .. nhit - 1 after a failed first try (out of line: about 2 % of
+// first tries fail at beta 6): delta of the first accepted one, -1 when all
+// fail.
+static __device__ __noinline__ float su3c_kp_retry(float inv_alpha, int nhit, Stream tries) {
+  for (int t = 1; t < nhit; ++t) {
+    float u[4], d;
+    tries.uniforms<float>(uint32_t(t), u);
+    if (kp_try_f32(u, inv_alpha, d)) return d;
+  }
+  return -1.f;
 }
 
 // The alpha = 0 case (Haar-random rotation), out of line: it is never taken at
@@ -306,7 +336,8 @@ static __device__ __noinline__ Quat<float> su3c_haar_rotation(Stream dir) { retu
 // Returns the link as stored (rows 0-1; row 2 not kept up to date).
 template <int FIELD, int KIND, int MU>
 __device__ __forceinline__ M3<float> su3c_update(const Ctx& a, int parity, int h, const LexSite& x,
-                                                 const M3<float>& A, M3<float> U) {
+                                                 const M3<float>& A, M3<float> U, const KpFirst* first = nullptr,
+                                                 uint32_t sweep = 0) {
   M3<float> Ut = U;
   if (FIELD == 2 && MU == 1) {
     Cx<float> b[3];
@@ -325,8 +356,6 @@ __device__ __forceinline__ M3<float> su3c_update(const Ctx& a, int parity, int h
     }
   }
   M3<float> W = su3c_mul3(Ut, A);
-  uint32_t sweep = 0;
-  if (KIND == KIND_HB) sweep = *a.sweep;
   unsigned exhausted = 0;
 #pragma unroll
   for (int sub = 0; sub < 3; ++sub) {
@@ -344,11 +373,19 @@ __device__ __forceinline__ M3<float> su3c_update(const Ctx& a, int parity, int h
         r = su3c_haar_rotation(dir);
       } else {
         const Stream tries = make_stream(a.k0, a.k1, uint32_t(x.s), sweep, MU, sub, KIND_TRY);
-        r = su3c_kp_rotation(alpha, a.nhit, tries, dir, qscale(w, rk));
-        if (r.q0 > 1.5f) {
-          ++exhausted;
-          continue;
+        const float inv_alpha = __fdividef(1.f, alpha);
+        float delta = first[sub].e * inv_alpha;
+        if (!(first[sub].a3 <= 1.f - 0.5f * delta)) {
+          delta = su3c_kp_retry(inv_alpha, a.nhit, tries);
+          if (delta < 0.f) {
+            ++exhausted;
+            continue;
+          }
         }
+        const float e = delta * (2.f - delta);
+        const float m = e * rsqrtf(e);
+        const KpFirst& f = first[sub];
+        r = qmul(Quat<float>{1.f - delta, -m * f.st * f.cp, -m * f.st * f.sp, m * f.ct}, qdag(qscale(w, rk)));
       }
     } else {
       if (n2 == 0.f) continue;
@@ -409,8 +446,18 @@ __global__ void __maxnreg__(KIND == KIND_HB          ? QCD_SU3_HB_MAXNREG
   if (frozen_link(a, MU, x.c[3])) return;
   pdl_wait();
   const int h = x.s >> 1;
+  KpFirst first[3];
+  uint32_t sweep = 0;
+  if (KIND == KIND_HB) {
+    sweep = *a.sweep;
+#pragma unroll
+    for (int sub = 0; sub < 3; ++sub)
+      first[sub] = su3c_kp_first(make_stream(a.k0, a.k1, uint32_t(x.s), sweep, MU, sub, KIND_TRY),
+                                 make_stream(a.k0, a.k1, uint32_t(x.s), sweep, MU, sub, KIND_DIR));
+  }
   const M3<float> A = su3c_staple<FIELD, MU>(a, parity, x);
-  su3c_update<FIELD, KIND, MU>(a, parity, h, x, A, su3c_full(su3c_load(a.links, a.g, MU, parity, h)));
+  su3c_update<FIELD, KIND, MU>(a, parity, h, x, A, su3c_full(su3c_load(a.links, a.g, MU, parity, h)), first,
+                               sweep);
 }
 
 // Last-pass phase (odd parity, MU >= 1) of a working sweep: update and
