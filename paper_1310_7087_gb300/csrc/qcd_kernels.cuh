@@ -723,6 +723,35 @@ __global__ void set_frozen_kernel(const Ctx a) {
   P::store(a.links, a.g, mu, parity_of(x), lex(a.g, x) >> 1, u);
 }
 
+// Sum of v over the block (any multiple of 32 threads), in a fixed order,
+// written by thread 0; every thread of the block must call it.  No FP64
+// arithmetic inside the warp (FP64 runs at a small fraction of the FP32 rate,
+// and five dependent FP64 adds per thread at the end of every CTA held its
+// warps): each shuffle level adds by Knuth's error-free TwoSum, t + e = s + s' exactly,
+// and carries the errors in c; lane 0 adds s + c in FP64.  The warp sum keeps
+// a relative error near 2^-48 (the rounding of c), as an FP64 sum of the
+// FP32 inputs would; the warps are then added in FP64.
+__device__ __forceinline__ void block_sum_f32(float v, double* out) {
+  __shared__ double sh[32];
+  float s = v, c = 0.f;
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) {
+    const float so = __shfl_down_sync(0xffffffffu, s, off), co = __shfl_down_sync(0xffffffffu, c, off);
+    const float t = s + so;
+    const float bp = t - s;
+    const float e = (s - (t - bp)) + (so - bp);
+    s = t;
+    c += co + e;
+  }
+  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = double(s) + double(c);
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double r = 0.0;
+    for (int w = 0; w < int(blockDim.x >> 5); ++w) r += sh[w];
+    *out = r;
+  }
+}
+
 // ---------------------------------------------------------------------------
 // Measurements: plaquette (spatial / temporal split) and Polyakov loop.
 // Products in the storage precision, sums in FP64: per-thread value, warp
@@ -856,7 +885,9 @@ static __global__ void __launch_bounds__(FINAL_THREADS)
 // Two strided steps per loop keep six loads of the one block in flight; the
 // per-thread sums are reduced by warp shuffles and then across the 32 warps,
 // all in a fixed order.
-static __global__ void __launch_bounds__(FINAL_THREADS) fused_final_kernel(const Ctx a, int grid) {
+// plane_scale multiplies the plane sums: 1 when the phase kernels summed
+// (1/N) Re Tr, 1/N when they summed Re Tr.
+static __global__ void __launch_bounds__(FINAL_THREADS) fused_final_kernel(const Ctx a, int grid, double plane_scale) {
   constexpr int NW = FINAL_THREADS / 32;
   __shared__ double sh[5][NW];
   const int nl = meas_poly_blocks(a.g);
@@ -904,6 +935,9 @@ static __global__ void __launch_bounds__(FINAL_THREADS) fused_final_kernel(const
     if (lane == 0) {
       const double V = 2.0 * double(a.g.Vh);
       const double V3 = double(a.g.Ns) * a.g.Ns * a.g.Ns;
+      s[0] *= plane_scale;
+      s[1] *= plane_scale;
+      s[2] *= plane_scale;
       const double sp = s[0] + s[1];
       a.meas_out[0] = (sp + s[2]) / (6.0 * V);
       a.meas_out[1] = sp / (3.0 * V);

@@ -176,16 +176,17 @@ __device__ __forceinline__ void su2c_block_sum(double v, double* out) {
 template <typename R, bool FIELD, int MU>
 __global__ void su2c_or_meas_kernel(const Ctx a, int parity) {
   const int h = blockIdx.x * blockDim.x + threadIdx.x;
-  double v = 0.0;
-  if (h < a.g.Vh) v = double(su2c_update<R, FIELD, KIND_OR_MEAS, MU, false>(a, parity, h, 0u));
-  su2c_block_sum(v, a.partials + fused_plaq_offset(a.g, MU) + blockIdx.x);
+  R v = R(0);
+  if (h < a.g.Vh) v = su2c_update<R, FIELD, KIND_OR_MEAS, MU, false>(a, parity, h, 0u);
+  if constexpr (sizeof(R) == 4) block_sum_f32(v, a.partials + fused_plaq_offset(a.g, MU) + blockIdx.x);
+  else su2c_block_sum(v, a.partials + fused_plaq_offset(a.g, MU) + blockIdx.x);
 }
 
 template <typename R>
 cudaError_t su2c_measure_fused_tail(const Ctx& a, int block, cudaStream_t st) {
   const int nl = meas_poly_blocks(a.g);
   measure_kernel<SU2Policy<R>, 0><<<nl, MEAS_THREADS, 0, st>>>(a, 0);  // Polyakov loop only
-  fused_final_kernel<<<1, FINAL_THREADS, 0, st>>>(a, int(grid_for(a.g.Vh, block)));
+  fused_final_kernel<<<1, FINAL_THREADS, 0, st>>>(a, int(grid_for(a.g.Vh, block)), 1.0);
   return cudaGetLastError();
 }
 

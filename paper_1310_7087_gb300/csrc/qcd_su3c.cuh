@@ -401,21 +401,6 @@ __device__ __forceinline__ M3<float> su3c_update(const Ctx& a, int parity, int h
   return U;
 }
 
-// Sum of v over the block (any multiple of 32 threads), in a fixed order,
-// written by thread 0.  Every thread of the block must call it.
-__device__ __forceinline__ void block_sum_any(double v, double* out) {
-  __shared__ double sh[32];
-#pragma unroll
-  for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(0xffffffffu, v, off);
-  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = v;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    double s = 0.0;
-    for (int w = 0; w < int(blockDim.x >> 5); ++w) s += sh[w];
-    *out = s;
-  }
-}
-
 // Register caps (64^3x16, per launch): overrelaxation QCD_SU3_PHASE_MAXNREG
 // (96); heat-bath 128 (0.2291 ms; 80 / 96 / 112 / 160 / 200: 0.2581 / 0.2359 /
 // 0.2392 / 0.2660 / 0.2640); the reunitarizing overrelaxation of the last
@@ -475,7 +460,7 @@ template <int FIELD, int MU>
 __global__ void __maxnreg__(QCD_SU3_MEAS_MAXNREG) su3c_or_meas_kernel(const Ctx a, int parity) {
   pdl_launch_dependents();
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  double v = 0.0;
+  float v = 0.f;
   if (i < a.g.Vh) {
     const LexSite x = lex_site_ytz(a.g, parity, i);
     pdl_wait();
@@ -501,9 +486,9 @@ __global__ void __maxnreg__(QCD_SU3_MEAS_MAXNREG) su3c_or_meas_kernel(const Ctx 
 #pragma unroll
         for (int k = 0; k < 3; ++k) U.e[r][k] = cmul_pm(U.e[r][k], b[k]);
     }
-    v = double(m3_retrace_mul(U, low)) / 3.0;
+    v = m3_retrace_mul(U, low);  // Re Tr; the final sums take the 1/3
   }
-  block_sum_any(v, a.partials + fused_plaq_offset(a.g, MU) + blockIdx.x);
+  block_sum_f32(v, a.partials + fused_plaq_offset(a.g, MU) + blockIdx.x);
 }
 
 // Polyakov loop of a working sweep's fused measurement: (1/3) Tr of the
@@ -535,7 +520,7 @@ static __global__ void __launch_bounds__(MEAS_THREADS) su3c_poly_kernel(const Ct
 
 inline cudaError_t su3c_measure_fused_tail(const Ctx& a, int block, cudaStream_t st) {
   su3c_poly_kernel<<<meas_poly_blocks(a.g), MEAS_THREADS, 0, st>>>(a);
-  fused_final_kernel<<<1, FINAL_THREADS, 0, st>>>(a, int(grid_for(a.g.Vh, block)));
+  fused_final_kernel<<<1, FINAL_THREADS, 0, st>>>(a, int(grid_for(a.g.Vh, block)), 1.0 / 3.0);
   return cudaGetLastError();
 }
 
