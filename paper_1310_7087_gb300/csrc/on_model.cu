@@ -423,7 +423,7 @@ int qcd_on_create(qcd_on** out, int N, int Ns, int Nt, double kappa, double lamb
   L->g.Ns = Ns;
   L->g.Nt = Nt;
   L->g.Vh = int(V / 2);
-  L->g.pow2 = geom_pow2_code(Ns, Nt);
+  geom_set_decode(L->g);
   L->g.plane = (L->g.Vh + 63) / 64 * 64;
   L->n_meas_blocks = int((V + ON_MEAS_THREADS - 1) / ON_MEAS_THREADS);
   const size_t field_bytes = size_t(2) * size_t(L->g.plane) * 16 * (precision == QCD_FP64_PLAIN ? 2 : 1);

@@ -510,7 +510,7 @@ int create_lattice(qcd_lattice** out, int group, int Ns, int Nt, double beta, in
   L->g.Ns = Ns;
   L->g.Nt = Nt;
   L->g.Vh = int(V / 2);
-  L->g.pow2 = qcd::geom_pow2_code(Ns, Nt);
+  qcd::geom_set_decode(L->g);
   L->g.plane = (L->g.Vh + 63) / 64 * 64;
   L->link_bytes = size_t(L->ops->comps) * 8 * size_t(L->g.plane) * 16;
   auto fail = [&](int rc) {

@@ -201,7 +201,7 @@ __device__ void batch_run(const BatchArgs& b, int li, const BatchLat& L, int j) 
   a.g.Vh = L.Vh;
   a.g.pow2 = ((L.Ns & (L.Ns - 1)) | (L.Nt & (L.Nt - 1))) == 0
                  ? (__ffs(L.Ns) - 1) | ((__ffs(L.Nt) - 1) << 8) | (1 << 16)
-                 : 0;  // as geom_pow2_code
+                 : 0;  // the power-of-two code of geom_set_decode (no multiply-high divisions here)
   a.g.plane = L.plane;
   a.beta = L.beta;
   a.k0 = b.seed_lo ^ L.kxor;

@@ -399,16 +399,30 @@ struct Site {
   int x, y, z, t;
 };
 
+// n / d for 0 <= n < 2^31 by the multiply-high of GeomH (m, s for d).
+__device__ __forceinline__ int div_mh(int n, uint32_t m, int s) { return int(__umulhi(uint32_t(n), m) >> s); }
+
 __device__ __forceinline__ Site site_of(const Geom& g, int parity, int h) {
   int r = 2 * h;
   Site c;
   int x0;
-  if (g.pow2) {  // the same decoding by shifts and masks (uniform branch)
+  if (g.pow2 & GEOM_POW2) {  // the same decoding by shifts and masks (uniform branch)
     const int ls = g.pow2 & 255, m = g.Ns - 1;
     x0 = r & m;
     c.y = (r >> ls) & m;
     c.z = (r >> (2 * ls)) & m;
     c.t = r >> (3 * ls);
+  } else if (g.mNs) {  // by multiply-high (uniform branch)
+    const int sN = (g.pow2 >> 17) & 31;
+    int q = div_mh(r, g.mNs, sN);
+    x0 = r - q * g.Ns;
+    r = q;
+    q = div_mh(r, g.mNs, sN);
+    c.y = r - q * g.Ns;
+    r = q;
+    q = div_mh(r, g.mNs, sN);
+    c.z = r - q * g.Ns;
+    c.t = q;
   } else {
     x0 = r % g.Ns;
     r /= g.Ns;
@@ -502,12 +516,23 @@ __device__ __forceinline__ LexSite lex_site_ytz(const Geom& g, int parity, int i
   int r = 2 * i;
   LexSite x;
   int x0;
-  if (g.pow2) {  // the same decoding by shifts and masks (uniform branch)
+  if (g.pow2 & GEOM_POW2) {  // the same decoding by shifts and masks (uniform branch)
     const int ls = g.pow2 & 255, lt = (g.pow2 >> 8) & 255, m = g.Ns - 1;
     x0 = r & m;
     x.c[1] = (r >> ls) & m;
     x.c[3] = (r >> (2 * ls)) & (g.Nt - 1);
     x.c[2] = r >> (2 * ls + lt);
+  } else if (g.mNs) {  // by multiply-high (uniform branch)
+    const int sN = (g.pow2 >> 17) & 31, sT = (g.pow2 >> 22) & 31;
+    int q = div_mh(r, g.mNs, sN);
+    x0 = r - q * g.Ns;
+    r = q;
+    q = div_mh(r, g.mNs, sN);
+    x.c[1] = r - q * g.Ns;
+    r = q;
+    q = div_mh(r, g.mNt, sT);
+    x.c[3] = r - q * g.Nt;
+    x.c[2] = q;
   } else {
     x0 = r % g.Ns;
     r /= g.Ns;

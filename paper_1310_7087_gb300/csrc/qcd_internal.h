@@ -12,18 +12,44 @@ struct GeomH {
   int Ns, Nt;
   int Vh;
   int pow2;  // log2(Ns) | log2(Nt) << 8 | 1 << 16 when Ns and Nt are powers of two
-             // (site decoding by shifts and masks), else 0 (by division)
+             // (site decoding by shifts and masks); otherwise the shifts of
+             // the divisions by Ns and Nt below in bits 17-21 and 22-26
   int64_t plane;
+  // Division of 0 <= n < 2^31 by Ns (Nt) as a multiply-high and a shift:
+  // n / d = umulhi(n, m) >> s with l = ceil(log2 d), s = l - 1 and
+  // m = ceil(2^(31 + l) / d) < 2^32.  Exact: n m / 2^(31 + l) exceeds n / d
+  // by less than n / 2^(31 + l) < 2^-l <= 1 / d, and the fraction of n / d is
+  // at most 1 - 1 / d.  0: decode by division.
+  uint32_t mNs, mNt;
 };
 
-inline int geom_pow2_code(int Ns, int Nt) {
+constexpr int GEOM_POW2 = 1 << 16;
+
+inline void geom_div_magic(uint32_t d, uint32_t* m, int* s) {
+  int l = 0;
+  while ((1u << l) < d) ++l;
+  *m = uint32_t(((uint64_t(1) << (31 + l)) + d - 1) / d);
+  *s = l - 1;
+}
+
+// Site-decoding fields of g for Ns, Nt >= 2: the power-of-two code, or the
+// multiply-high divisions.
+inline void geom_set_decode(GeomH& g) {
   auto lg = [](int n) {
     int l = 0;
     while ((1 << l) < n) ++l;
     return (1 << l) == n ? l : -1;
   };
-  const int ls = lg(Ns), lt = lg(Nt);
-  return ls >= 0 && lt >= 0 ? (ls | (lt << 8) | (1 << 16)) : 0;
+  const int ls = lg(g.Ns), lt = lg(g.Nt);
+  g.mNs = g.mNt = 0;
+  if (ls >= 0 && lt >= 0) {
+    g.pow2 = ls | (lt << 8) | GEOM_POW2;
+    return;
+  }
+  int sN = 0, sT = 0;
+  geom_div_magic(uint32_t(g.Ns), &g.mNs, &sN);
+  geom_div_magic(uint32_t(g.Nt), &g.mNt, &sT);
+  g.pow2 = (sN << 17) | (sT << 22);
 }
 
 // Everything a kernel launch needs for one lattice.  Device pointers only.

@@ -93,7 +93,7 @@ extern "C" int qcd_measure_noalloc(const void* links, size_t link_bytes, int gro
   g.Ns = Ns;
   g.Nt = Nt;
   g.Vh = int(V / 2);
-  g.pow2 = qcd::geom_pow2_code(Ns, Nt);
+  qcd::geom_set_decode(g);
   // The storage holds comps x 4 directions x 2 parities arrays of `plane`
   // 16-byte vectors each; the padding of `plane` depends on how the lattice
   // was made, so it is read off the buffer size.
