@@ -2,7 +2,9 @@
 FP32-compressed links, in the launch configuration the benchmark times
 (autotuned block size, graph-launched sweeps).  The oracle recomputes sampled
 links one by one from the same pre-phase state; untouched links must be
-bit-identical; the plaquette of one configuration must agree to 1e-6."""
+bit-identical; the plaquette of one configuration must agree to 1e-6.  The
+same on 60^3 x 10 (2.2M sites), whose extents are not powers of two, so the
+kernels decode sites by multiply-high and shift rather than by masks."""
 import numpy as np
 import pytest
 
@@ -36,8 +38,10 @@ def parity_sites(Ns, Nt, parity, n, rng):
     return out
 
 
-def test_full_size_sampled_phases(q):
-    w = workloads.SU3_64x16
+@pytest.mark.parametrize("Ns,Nt,n_samples", [(64, 16, 1500), (60, 10, 500)])
+def test_full_size_sampled_phases(q, Ns, Nt, n_samples):
+    import dataclasses
+    w = dataclasses.replace(workloads.SU3_64x16, Ns=Ns, Nt=Nt)
     lat = q.Lattice(3, w.Ns, w.Nt, w.beta, w.flux, FP32_COMPRESSED, HOT, w.seed)
     lat.sweep(1, w.n_or, w.seed)
     U0 = lat.get_links()
@@ -51,7 +55,7 @@ def test_full_size_sampled_phases(q):
     assert np.abs(np.array(gl) - ol).max() <= 1e-6, (gl, ol)
 
     rng = np.random.default_rng(0)
-    # FP32 bar pooled over the 7500 samples: none beyond 1e-4, at most one
+    # FP32 bar pooled over the 5 x n_samples samples: none beyond 1e-4, at most one
     # beyond 1e-5 (an overrelaxation reflection with a small subgroup norm
     # amplifies FP32 rounding past 1e-5 about once in 10^5 updates).  The last
     # two phases are kernels of a sweep's last overrelaxation pass: each
@@ -62,7 +66,7 @@ def test_full_size_sampled_phases(q):
                              (q.QCD_OVERRELAX_REUNIT, 0, 1), (q.QCD_OVERRELAX_MEASURE, 1, 2)]:
         lat.phase(kind, parity, mu, w.seed)
         U1 = lat.get_links()
-        sites = parity_sites(w.Ns, w.Nt, parity, 1500, rng)
+        sites = parity_sites(w.Ns, w.Nt, parity, n_samples, rng)
         for s in sites:
             if kind in (q.QCD_OVERRELAX_REUNIT, q.QCD_OVERRELAX_MEASURE):
                 ref = oracle.reunitarize_matrix(orc.link_update(q.QCD_OVERRELAX, s, mu, w.seed)[0])
