@@ -178,8 +178,10 @@ int qcd_sweep(qcd_lattice *lat, int n_heatbath, int n_overrelax, uint64_t seed);
  * effective-link field mode, the plaquette sums are fused into the last
  * overrelaxation pass: after the pass each plaquette of plane (mu, nu < mu)
  * contains exactly one odd mu-link, so the odd phases mu = 1, 2, 3 add
- * (1/3) Re Tr(Ut A_nu) for nu < mu over their updated links (A_nu the staples
- * of plane (mu, nu)) and no separate pass over the links is needed; otherwise
+ * Re Tr(Ut A_nu) for nu < mu over their updated links (A_nu the staples of
+ * plane (mu, nu); each warp adds its threads' FP32 values by error-free
+ * TwoSum and finishes in FP64, the block adds its warps in FP64, and the final
+ * sums take the 1/3) and no separate pass over the links is needed; otherwise
  * the measurement kernels run after the sweeps.  wait = 1: returns after the
  * results are on the host; wait = 0: host_out (page-locked for overlap) is
  * filled once the stream is synchronized. */
@@ -197,10 +199,12 @@ int qcd_working_sweep(qcd_lattice *lat, int n_heatbath, int n_overrelax,
  *   QCD_OVERRELAX_MEASURE         a plane-summing phase of a working sweep's
  *                                 last pass (parity 1, mu = 1, 2, 3; else
  *                                 QCD_ERR_INVALID_ARG): as QCD_OVERRELAX_REUNIT,
- *                                 and (1/N) Re Tr of every plaquette of the
- *                                 planes (mu, nu < mu) is summed, through the
- *                                 updated link of each, into the lattice's
- *                                 measurement scratch; QCD_ERR_NOT_SUPPORTED
+ *                                 and Re Tr of every plaquette of the planes
+ *                                 (mu, nu < mu) is summed (SU(2): (1/2) Re Tr),
+ *                                 through the updated link of each, into the
+ *                                 lattice's measurement scratch (the SU(3)
+ *                                 1/3 is taken in the final sums);
+ *                                 QCD_ERR_NOT_SUPPORTED
  *                                 where qcd_working_sweep does not fuse its
  *                                 measurement (FP64 SU(3), frozen mode).
  * After the eight phases of a last pass run this way (QCD_OVERRELAX_REUNIT for
