@@ -709,7 +709,9 @@ def main():
     nbytes = q.qcd_link_bytes(h)
     host = torch.empty(nbytes, dtype=torch.uint8, pin_memory=True)
     q.qcd_copy_links_out(h, host.data_ptr(), nbytes)
-    e2e_steps, e2e_warmup = 40, 4
+    # as many timed steps as the device-timed pass (at least 40): the first
+    # step's upload has no sweep before it to hide behind
+    e2e_steps, e2e_warmup = max(40, args.steps), 4
     stream2 = torch.cuda.Stream()
     lat2 = q.Lattice(w.group, w.Ns, w.Nt, w.beta, w.flux, prec, q.QCD_HOT, seed, stream2)
     pipe = [h, lat2.h]
