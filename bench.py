@@ -723,15 +723,23 @@ def main():
     streams = [stream, stream2]
     done = [torch.cuda.Event(), torch.cuda.Event()]
 
-    def pipeline(first, n):
+    # device events around every timed sweep: where the end-to-end time goes
+    sweep_ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+                for _ in range(e2e_steps)]
+
+    def pipeline(first, n, events=None):
         for i in range(first, first + n):
             k = i % 2
             q.qcd_copy_links_in(pipe[k], host.data_ptr(), nbytes)
             if i > first:
                 streams[k].wait_event(done[1 - k])
+            if events:
+                events[i - first][0].record(streams[k])
             q.qcd_working_sweep(pipe[k], 1, w.n_or, seed, results.data_ptr() + i * results.stride(0) * 8,
                                 wait=False)
             done[k].record(streams[k])
+            if events:
+                events[i - first][1].record(streams[k])
 
     # untimed warm-up steps of the same pipeline on the same buffers (the first
     # pipelined steps of a fresh process measured up to 20 % slower)
@@ -739,11 +747,17 @@ def main():
     torch.cuda.synchronize()
     if dist:
         dist.barrier()
+    clocks_e2e = ClockSampler(local)
+    time.sleep(0.3)
+    clocks_e2e.start()
     t0 = time.perf_counter()
-    pipeline(e2e_warmup, e2e_steps)
+    pipeline(e2e_warmup, e2e_steps, sweep_ev)
     torch.cuda.synchronize()
     t_e2e = time.perf_counter() - t0
+    clocks_e2e.stop()
     assert bool(torch.all(results[:, 0] > 0)), "a pipelined measurement did not arrive"
+    sweep_ms = [a.elapsed_time(b) for a, b in sweep_ev]
+    first_to_last_ms = sweep_ev[0][0].elapsed_time(sweep_ev[-1][1])
     lat2.close()
     if dist:
         t = torch.tensor([t_e2e], device="cuda")
@@ -751,6 +765,9 @@ def main():
         t_e2e = float(t.item())
     e2e = {"value": lu_per_step * e2e_steps * world / t_e2e, "unit": UNIT, "h2d_bytes_per_step": nbytes,
            "d2h_bytes_per_step": 5 * 8, "steps": e2e_steps,
+           "sweep_ms_mean": sum(sweep_ms) / len(sweep_ms), "sweep_ms_max": max(sweep_ms),
+           "first_to_last_sweep_ms": first_to_last_ms, "host_ms": 1e3 * t_e2e,
+           "clocks": clocks_e2e.summary(),
            "pipeline": "each step uploads a configuration in the library's device storage layout "
                        "(qcd_copy_links_in of the qcd_link_bytes bytes qcd_copy_links_out gave) from pinned "
                        "host memory and reads its five measured doubles back (qcd_working_sweep into pinned "
